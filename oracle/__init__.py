@@ -1,0 +1,27 @@
+"""FP64 CPU oracle for least-misfit gridding and degridding (Ye, Gull, Tan & Nikolic 2019).
+
+TEST INFRASTRUCTURE ONLY. Nothing in the product imports this package: only ``tests/``,
+``__graft_entry__.smoke()`` and the ``cpu_baseline`` / ``--impl reference`` legs of
+``bench.py`` may call it. It shares no code, table, constant generator or helper with the
+CUDA library under ``paper_1906_07102_gb300/``.
+
+Modules
+-------
+``design``   the least-misfit function: quadrature nodes, the per-offset linear systems
+             (normal equations with Cholesky, or least squares with QR), the map error
+             l(x) and the integrated misfit E, the Levenberg-Marquardt optimisation of the
+             correcting function h, the look-up table and the grid-correction factors
+             (Section 2.1, Appendices A, B, E, F).
+``imaging``  the support rule, table lookup, gridding, FFT dirty image with correction and
+             crop, its adjoint (pad, correct, FFT, degrid), the brute-force DFT references
+             and the Cauchy-Schwarz misfit bound (Section 2.1 Eqs. 3-9, Section 4).
+
+Everything is plain numpy/scipy in float64, written step by step in the paper's order.
+Library primitives used as single steps: ``scipy.optimize.leastsq`` (MINPACK
+Levenberg-Marquardt, the routine the paper names in Appendix A), ``scipy.linalg`` Cholesky
+and triangular solves, ``numpy.linalg.qr`` (Householder QR, Appendix B) and ``numpy.fft``.
+
+Parity status: the exact values of C(u) and h(x) are **parity unpinned** -- the paper
+prints no values (its figures are lost). They are pinned indirectly by stationarity,
+by the paper's ordering and bound claims and by route agreement (see tests/test_oracle_*.py).
+"""

@@ -1,0 +1,234 @@
+"""Pins for the oracle's least-misfit design (CPU only).
+
+Each test checks the FP64 oracle against something other than itself: a second solution
+route, a stationarity condition, the paper's stated orderings and levels, closed-form
+properties (symmetry, identities) or convergence rates.
+"""
+import functools
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import design as D
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_claims.json")
+X0P = 0.25  # the paper's recommended x0 (half width); the API's kept fraction 0.5
+
+
+@functools.lru_cache(maxsize=None)
+def h_opt(W, x0p=X0P):
+    return D.least_misfit_h(W, x0p)
+
+
+def claims():
+    with open(GOLDEN) as f:
+        return json.load(f)
+
+
+def fine_E(C_of_offsets, W, x0p=X0P, nx=257, ns=4096):
+    """E of Eq. 16 on fine x and s rules with the optimal h, for any gridding function."""
+    sn, sw = D.uniform_s_rule(ns)
+    xf = np.linspace(-x0p, x0p, nx)
+    tw = np.full(nx, xf[1] - xf[0])
+    tw[[0, -1]] *= 0.5
+    ell, _ = D.map_error(lambda s: C_of_offsets(D.support_offsets(s, W)), W, xf, sn, sw)
+    return float(tw @ ell) / (2 * x0p)
+
+
+def lm_fine_E(W, x0p=X0P):
+    h = h_opt(W, x0p)
+    sn, sw = D.uniform_s_rule(4096)
+    xf = np.linspace(-x0p, x0p, 257)
+    tw = np.full(257, xf[1] - xf[0])
+    tw[[0, -1]] *= 0.5
+    ell, _ = D.map_error(lambda s: D.exact_C(h, W, x0p, s), W, xf, sn, sw)
+    return float(tw @ ell) / (2 * x0p), xf, ell
+
+
+@pytest.mark.parametrize("W", [4, 7])
+def test_cholesky_qr_lstsq_agree(W):
+    """Normal equations (Eq. 18) and the least-squares form (Appendix B) give the same C;
+    LAPACK's lstsq is a third route."""
+    x, tau, s = D.design_nodes(X0P)
+    h = D.mirror_h(h_opt(W))
+    C1 = D.solve_C_cholesky(h, x, tau, W, s)
+    C2 = D.solve_C_qr(h, x, tau, W, s)
+    C3 = np.empty_like(C2)
+    for k, sk in enumerate(s):
+        M, rhs = D.least_squares_system(h, x, tau, W, sk)
+        C3[k] = np.linalg.lstsq(M, rhs, rcond=None)[0]
+    scale = np.abs(C2).max()
+    assert np.abs(C1 - C2).max() < 1e-9 * scale
+    assert np.abs(C3 - C2).max() < 1e-11 * scale
+
+
+@pytest.mark.parametrize("W", [3, 5, 7])
+def test_lm_optimum_is_stationary_in_h(W):
+    """At the joint optimum the per-node optimal h for the current C (Eq. 12 on the nodes)
+    reproduces h: one alternating-minimisation step leaves it unchanged."""
+    x, tau, s = D.design_nodes(X0P)
+    h = D.mirror_h(h_opt(W))
+    C = D.solve_C(h, x, tau, W, s)
+    a = D.footprint_sum(C, W, s, x)
+    h_new = a.real.sum(0) / (np.abs(a) ** 2).sum(0)
+    h_new /= h_new[x.size // 2]
+    assert np.max(np.abs(h_new - h) / h) < 1e-6
+
+
+def test_lm_optimum_is_a_minimum():
+    """Random perturbations of h(x_1..x_Ng) never lower E."""
+    W = 6
+    h = h_opt(W)
+    E0 = D.design_E(h, W, X0P)
+    g = np.random.default_rng(0)
+    for _ in range(20):
+        dh = np.concatenate([[0.0], g.standard_normal(h.size - 1)]) * 1e-4
+        assert D.design_E(h * (1 + dh), W, X0P) >= E0 * (1 - 1e-9)
+
+
+def test_w7_map_error_level():
+    """W = 7, x0 = 0.25 reaches a map error of order 1e-14 over the kept field (Section 2.2)."""
+    level = claims()["lm_W7_x0_0p25_map_error_order"]["value"]
+    E, xf, ell = lm_fine_E(7)
+    assert E < 2 * level
+    inner = np.abs(xf) <= 0.95 * X0P
+    assert ell[inner].max() < 5 * level
+    assert E > 1e-3 * level  # it is not an exact interpolator either
+
+
+def test_map_error_flat_inside_then_rising():
+    """For several x0, l(x) stays small across |x| <= x0 and rises quickly beyond it
+    (Section 2.2's x0 sweep, shown there for W = 8; W = 6 here to keep the test short)."""
+    W = 6
+    sn, sw = D.uniform_s_rule(2048)
+    for x0p in (0.2, 0.25, 0.3):
+        h = h_opt(W, x0p)
+        xs = np.array([0.0, 0.5 * x0p, 0.9 * x0p, x0p + 0.1])
+        ell, _ = D.map_error(lambda s: D.exact_C(h, W, x0p, s), W, xs, sn, sw)
+        assert ell[3] > 1e3 * ell[:3].max()
+
+
+def test_E_decreases_with_W():
+    Es = [D.design_E(h_opt(W), W, X0P) for W in range(1, 9)]
+    assert all(b < a for a, b in zip(Es, Es[1:]))
+
+
+@pytest.mark.parametrize("W", [2, 3, 5, 7, 8])
+def test_h_increases_on_kept_field(W):
+    """h(x) increases monotonically on [0, x0] for W >= 2 (Section 3)."""
+    h = h_opt(W)
+    assert np.all(np.diff(h) > 0)
+
+
+def test_least_misfit_beats_common_functions():
+    """E of the least-misfit function is below that of nearest-neighbour (W = 1),
+    linear (W = 2), truncated sinc, Gaussian and Gaussian-times-sinc (W = 8) gridding
+    functions, each with its own optimal correction (Section 2.2 comparison)."""
+    E8 = lm_fine_E(8)[0]
+    for f in (np.sinc, lambda d: np.exp(-d ** 2),
+              lambda d: np.exp(-(np.abs(d) / 2.52) ** 2) * np.sinc(d / 1.55)):
+        assert E8 < fine_E(f, 8)
+    assert lm_fine_E(1)[0] < fine_E(lambda d: np.ones_like(d), 1)
+    assert lm_fine_E(2)[0] < fine_E(lambda d: 1 - np.abs(d), 2)
+
+
+@pytest.mark.parametrize("W", [6, 7, 8])
+def test_at_least_100x_below_spheroidal(W):
+    """Spheroidal function (alpha = 1, scipy's pro_ang1, c = pi W / 2) has at least 100
+    times the integrated map error at equal W (Abstract, Sections 2.2, 4.1)."""
+    from scipy.special import pro_ang1
+    alpha = 1
+    c = np.pi * W / 2
+
+    def pswf(d):
+        eta = np.clip(2 * d / W, -1, 1)
+        return pro_ang1(alpha, alpha, c, eta)[0] * (1 - eta ** 2) ** (alpha / 2)
+
+    factor = claims()["lm_vs_spheroidal_min_factor"]["value"]
+    assert fine_E(pswf, W) > factor * lm_fine_E(W)[0]
+
+
+def test_small_W_shapes():
+    """Appendix C: for W = 1 the function is close to but not exactly 1, heavier on a grid
+    point than midway; for W = 2 it is close to but not exactly 1 - |u|, and does not
+    reach zero at |u| = 1."""
+    s = np.linspace(0, 1, 201)[:-1]
+    C1 = D.exact_C(h_opt(1), 1, X0P, s)[:, 0]          # d = s - 1/2
+    assert np.all(np.abs(C1 - 1) < 0.2) and np.std(C1) > 1e-4
+    assert C1[100] > C1[0]                             # d = 0 vs d = -1/2
+    C2 = D.exact_C(h_opt(2), 2, X0P, s)                # d = (-1 + s, s)
+    d = D.support_offsets(s, 2)
+    dev = np.abs(C2 - (1 - np.abs(d)))
+    assert 1e-4 < dev.max() < 0.2
+    assert abs(C2[0, 0]) > 1e-4                        # C(-1) != 0
+
+
+def test_table_mirror_symmetry_and_size():
+    """C is even, so row i of the table mirrors row Ms - i (the paper stores half,
+    Section 5.2); the table has W*(Ms+1) entries (W*Ms plus one guard row)."""
+    for W, Ms in ((7, 1000), (8, 64), (3, 100)):
+        T = D.lm_table(h_opt(W), W, X0P, Ms)
+        assert T.shape == (Ms + 1, W)
+        assert np.abs(T[::-1, ::-1] - T).max() < 1e-11 * np.abs(T).max()
+    c = claims()
+    assert c["casa_level_table_entries"]["W"] * c["casa_level_table_entries"]["Ms"] == \
+        c["casa_level_table_entries"]["value"]
+    half = 7 * 10 ** 6 / 2
+    assert half == c["half_table_floats_W7_Ms1e6"]["value"]
+    assert abs(half * 4 / 2 ** 20 - c["half_table_floats_W7_Ms1e6"]["megabytes"]) < 0.01
+
+
+def test_interpolation_error_order():
+    """Table error against the exact function falls as Ms^-1 (nearest) and Ms^-2
+    (linear) (Appendix F)."""
+    W = 7
+    h = h_opt(W)
+    s = (np.arange(6000) + 0.37) / 6000
+    exact = D.exact_C(h, W, X0P, s)
+    errs = {0: [], 1: []}
+    for Ms in (50, 100, 200):
+        T = D.lm_table(h, W, X0P, Ms)
+        for interp in (0, 1):
+            errs[interp].append(np.abs(D.table_weights(T, Ms, s, interp) - exact).max())
+    p0 = np.log2(errs[0][0] / errs[0][2]) / 2
+    p1 = np.log2(errs[1][0] / errs[1][2]) / 2
+    assert abs(p0 - 1) < 0.15
+    assert abs(p1 - 2) < 0.15
+
+
+def test_optimal_correction_identities():
+    """At h = c/D, l = 1 - h c (Eq. 20); inside the kept field h_opt and 1/c agree closely
+    (Section 3)."""
+    W, Ms = 7, 1000
+    T = D.lm_table(h_opt(W), W, X0P, Ms)
+    sn, sw = D.uniform_s_rule(20000)
+    xs = np.linspace(0, 0.45, 10)
+    fun = lambda s: D.table_weights(T, Ms, s, D.INTERP_LINEAR)
+    ell, h = D.map_error(fun, W, xs, sn, sw)
+    a = D.footprint_sum(fun(sn), W, sn, xs)
+    c = sw @ a.real
+    np.testing.assert_allclose(ell, 1 - h * c, atol=1e-13)
+    inside = xs <= X0P
+    assert np.max(np.abs(h[inside] * c[inside] - 1)) < 1e-6
+
+
+@pytest.mark.parametrize("interp", [0, 1])
+def test_correction_quadrature(interp):
+    """Piecewise Gauss-Legendre (per table piece) against a dense midpoint rule."""
+    W, Ms = 5, 40
+    T = D.lm_table(h_opt(W), W, X0P, Ms)
+    xs = np.linspace(-0.25, 0.25, 9)
+    h_gl = D.correction_factors(T, Ms, interp, W, xs)
+    sn, sw = D.uniform_s_rule(400000)
+    _, h_mid = D.map_error(lambda s: D.table_weights(T, Ms, s, interp), W, xs, sn, sw)
+    np.testing.assert_allclose(h_gl, h_mid, rtol=2e-7)
+
+
+def test_node_count_convergence():
+    """Doubling Ng changes the W = 7 optimum's E by less than 10% (reading of Appendix A's
+    node counts)."""
+    E32 = D.design_E(h_opt(7), 7, X0P)
+    E64 = D.design_E(D.least_misfit_h(7, X0P, Ng=64), 7, X0P, Ng=64)
+    assert abs(E64 - E32) < 0.1 * E32

@@ -1,0 +1,199 @@
+"""Pins for the oracle's gridding, imaging and degridding (CPU only).
+
+The FFT path is checked against brute-force DFTs within the paper's exact per-pixel
+Cauchy-Schwarz bound, against a closed form for a single visibility, against explicit
+double sums on tiny grids and against the adjoint identity; the support rule is checked
+against exact rational arithmetic.
+"""
+import functools
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import design as D
+from oracle import imaging as I
+from paper_1906_07102_gb300 import synthetic as S
+
+HERE = os.path.dirname(__file__)
+
+
+@functools.lru_cache(maxsize=None)
+def table(W, x0p, Ms):
+    h = D.least_misfit_h(W, x0p)
+    return D.lm_table(h, W, x0p, Ms)
+
+
+def setup(n_img, N, W, Ms, interp, nvis, seed=0, radius=None):
+    x0p = n_img / (2.0 * N)
+    T = table(W, x0p, Ms)
+    x = I.pixel_coords(n_img, N)
+    hvec = D.correction_factors(T, Ms, interp, W, x)
+    uv = S.disk_uniform(nvis, (radius or 0.45) * N, seed)
+    return T, x, hvec, uv
+
+
+@pytest.mark.parametrize("W", [1, 2, 3, 4, 7, 8, 12, 16])
+def test_support_rule_exact(W):
+    """n_start = ceil(u - W/2) and the W points n_start..n_start+W-1 are exactly the set
+    {n : u - W/2 <= n < u + W/2} (Eq. 6), with u quantised to 2^-32 cell."""
+    g = np.random.default_rng(W)
+    u = np.concatenate([g.uniform(-3000, 3000, 300), np.round(g.uniform(-50, 50, 50)),
+                        np.round(g.uniform(-50, 50, 50)) + 0.5, [0.0, -0.5, 0.5, 2.0 ** -33, -2.0 ** -33]])
+    n0, S_, valid = I.support_rule(u, W)
+    assert valid.all()
+    for uk, nk, sk in zip(u, n0, S_):
+        uq = Fraction(int(np.rint(np.ldexp(uk, 32))), 1 << 32)
+        lo, hi = uq - Fraction(W, 2), uq + Fraction(W, 2)
+        members = [n for n in range(int(lo) - 2, int(hi) + 3) if lo <= n < hi]
+        assert members == list(range(int(nk), int(nk) + W))
+        assert Fraction(int(sk), 1 << 32) == nk - lo
+        assert 0 <= sk < (1 << 32)
+
+
+def test_invalid_positions_are_dropped():
+    _, _, valid = I.support_rule(np.array([1.0, np.nan, np.inf, 2.0 ** 31, -2.0 ** 30, 5.5]), 7)
+    assert valid.tolist() == [True, False, False, False, False, True]
+
+
+def test_fft_image_equals_explicit_sum():
+    """numpy FFT use matches Eq. 4's double sum (before correction) on a tiny grid."""
+    N = 8
+    g = np.random.default_rng(1)
+    G = g.standard_normal((N, N)) + 1j * g.standard_normal((N, N))
+    F = I.fft_image(G)
+    n = np.arange(N) - N // 2
+    for qy in range(N):
+        for qx in range(N):
+            ref = sum(G[iy, ix] * np.exp(2j * np.pi * (n[ix] * qx + n[iy] * qy) / N)
+                      for iy in range(N) for ix in range(N))
+            assert abs(F[qy, qx] - ref) < 1e-11
+
+
+def test_model_grid_equals_explicit_sum():
+    N = 8
+    g = np.random.default_rng(2)
+    P = g.standard_normal((N, N)) + 1j * g.standard_normal((N, N))
+    Gm = I.model_grid(P)
+    n = np.arange(N) - N // 2
+    for iy in range(N):
+        for ix in range(N):
+            ref = sum(P[qy, qx] * np.exp(-2j * np.pi * (n[ix] * qx + n[iy] * qy) / N)
+                      for qy in range(N) for qx in range(N))
+            assert abs(Gm[iy, ix] - ref) < 1e-11
+
+
+@pytest.mark.parametrize("W,Ms,interp", [(3, 100, 0), (7, 1000, 1), (4, 50, 1)])
+def test_dirty_image_within_bound(W, Ms, interp):
+    """|I_fft - I_DFT|^2 <= (sum w |V|^2)(sum w |1 - h h a a'|^2) at every pixel (Eq. 8)."""
+    n_img, N, nvis = 32, 64, 400
+    T, x, hvec, uv = setup(n_img, N, W, Ms, interp, nvis)
+    g = np.random.default_rng(3)
+    vis = S.complex_normal(nvis, 0)
+    w = g.uniform(0.5, 2.0, nvis)
+    plan = I.Plan(uv[:, 0], uv[:, 1], W, N, single_precision_s=False)
+    img = I.dirty_image(plan, T, Ms, interp, hvec, n_img, vis, w)
+    ref = I.dft_dirty_image(uv[:, 0], uv[:, 1], vis, w, x, x)
+    bound = I.image_bound(plan, T, Ms, interp, uv[:, 0], uv[:, 1], vis, w, x, x, hvec)
+    err2 = np.abs(img - ref) ** 2
+    # slack: float64 round-off of sums of ~1e3 unit terms and the 2^-33 cell quantisation
+    slack = 1e-20 * np.sum(np.abs(vis) ** 2) * nvis
+    assert np.all(err2 <= bound * (1 + 1e-9) + slack)
+    assert np.sqrt(err2.mean()) > 0  # not trivially exact
+
+
+def test_single_visibility_closed_form():
+    """For one visibility the dirty image is h(x)h(y) sum_i C_i e^{i2pi(n0+i)x}
+    sum_j C_j e^{i2pi(m0+j)y} V (Eqs. 4-5 with one term)."""
+    n_img, N, W, Ms = 32, 64, 7, 1000
+    T, x, hvec, _ = setup(n_img, N, W, Ms, 1, 1)
+    for u, v in [(3.3, -7.8), (-31.7, 30.2), (0.5, 0.0)]:
+        plan = I.Plan(np.array([u]), np.array([v]), W, N, single_precision_s=False)
+        V = np.array([0.3 - 1.1j])
+        img = I.dirty_image(plan, T, Ms, 1, hvec, n_img, V)
+        Cu, Cv = plan.weights(T, Ms, 1)
+        ax = (Cu[0][:, None] * np.exp(2j * np.pi * (plan.n0[0] + np.arange(W))[:, None] * x[None, :])).sum(0)
+        ay = (Cv[0][:, None] * np.exp(2j * np.pi * (plan.m0[0] + np.arange(W))[:, None] * x[None, :])).sum(0)
+        ref = V[0] * (hvec * ay)[:, None] * (hvec * ax)[None, :]
+        np.testing.assert_allclose(img, ref, atol=1e-12)
+
+
+def test_adjoint_identity():
+    """<dirty(V), I> = <V, w * predict(I)> with <a,b> = sum conj(a) b (Sections 2.1, 4)."""
+    n_img, N, W, Ms, nvis = 48, 96, 5, 200, 700
+    T, x, hvec, uv = setup(n_img, N, W, Ms, 1, nvis, radius=0.5)
+    g = np.random.default_rng(4)
+    vis = S.complex_normal(nvis, 1)
+    w = g.uniform(0.1, 3.0, nvis)
+    img = S.random_image(n_img, 2)
+    plan = I.Plan(uv[:, 0], uv[:, 1], W, N, single_precision_s=False)
+    lhs = np.vdot(I.dirty_image(plan, T, Ms, 1, hvec, n_img, vis, w), img)
+    rhs = np.vdot(vis, w * I.predict_vis(plan, T, Ms, 1, hvec, img))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+@pytest.mark.parametrize("W,Ms,interp", [(3, 100, 0), (7, 1000, 1)])
+def test_predict_within_bound(W, Ms, interp):
+    n_img, N, nvis = 32, 64, 60
+    T, x, hvec, uv = setup(n_img, N, W, Ms, interp, nvis)
+    img = S.random_image(n_img, 5)
+    plan = I.Plan(uv[:, 0], uv[:, 1], W, N, single_precision_s=False)
+    pred = I.predict_vis(plan, T, Ms, interp, hvec, img)
+    ref = I.dft_predict(uv[:, 0], uv[:, 1], img, x, x)
+    bound = I.predict_bound(plan, T, Ms, interp, uv[:, 0], uv[:, 1], img, x, x, hvec)
+    slack = 1e-20 * np.sum(np.abs(img) ** 2) * img.size
+    assert np.all(np.abs(pred - ref) ** 2 <= bound * (1 + 1e-9) + slack)
+
+
+def test_wrap_at_grid_edge():
+    """Support points beyond the grid edge wrap modulo N; exact at pixel centres."""
+    n_img, N, W, Ms = 16, 32, 7, 500
+    T, x, hvec, _ = setup(n_img, N, W, Ms, 1, 1)
+    uv = np.array([[N / 2 - 1.2, -N / 2 + 0.7], [-N / 2 + 0.1, N / 2 - 2.9]])
+    vis = np.array([1.0 + 0.5j, -0.7 + 0.2j])
+    plan = I.Plan(uv[:, 0], uv[:, 1], W, N, single_precision_s=False)
+    img = I.dirty_image(plan, T, Ms, 1, hvec, n_img, vis)
+    direct = I.dirty_pixels_direct(plan, T, Ms, 1, np.tile(hvec, n_img), np.repeat(hvec, n_img), vis, None,
+                                   np.tile(x, n_img), np.repeat(x, n_img))
+    np.testing.assert_allclose(img.ravel(), direct, atol=1e-12)
+
+
+def test_weights_are_linear():
+    n_img, N, W, Ms, nvis = 16, 32, 4, 100, 50
+    T, x, hvec, uv = setup(n_img, N, W, Ms, 1, nvis)
+    vis = S.complex_normal(nvis, 3)
+    w = np.random.default_rng(5).uniform(0, 2, nvis)
+    plan = I.Plan(uv[:, 0], uv[:, 1], W, N)
+    np.testing.assert_allclose(I.grid(plan, T, Ms, 1, vis, w), I.grid(plan, T, Ms, 1, vis * w), atol=1e-13)
+
+
+def test_testcard_sky_error_below_bound_and_single_precision():
+    """The paper's 34-source test card (Appendix D), at a quarter of its pixel offsets,
+    imaged with W = 7, x0 = 0.25, linear lookup at Ms = 1000: FFT image error against the
+    DFT stays under the bound and near single precision over the kept field (Section 4)."""
+    src = np.loadtxt(os.path.join(HERE, "golden", "testcard_34.txt"))
+    n_img, N, W, Ms, nvis = 256, 512, 7, 1000, 3000
+    T, x, hvec, uv = setup(n_img, N, W, Ms, 1, nvis, seed=7)
+    xs, ys = src[:, 1] / 4 / N, src[:, 2] / 4 / N
+    vis = (src[:, 3][None, :] * np.exp(-2j * np.pi * (uv[:, :1] * xs[None, :] + uv[:, 1:] * ys[None, :]))).sum(1)
+    plan = I.Plan(uv[:, 0], uv[:, 1], W, N, single_precision_s=False)
+    img = I.dirty_image(plan, T, Ms, 1, hvec, n_img, vis)
+    rows = np.arange(0, n_img, 16)
+    ref = I.dft_dirty_image(uv[:, 0], uv[:, 1], vis, None, x, x[rows])
+    err = img[rows] - ref
+    assert np.sqrt(np.mean(np.abs(err) ** 2)) < 1e-6 * np.sqrt(np.mean(np.abs(ref) ** 2))
+    bound = I.image_bound(plan, T, Ms, 1, uv[:, 0], uv[:, 1], vis, None, x, x[rows[::4]], hvec, hvec[rows[::4]])
+    assert np.all(np.abs(err[::4]) ** 2 <= bound * (1 + 1e-9) + 1e-20 * np.sum(np.abs(vis) ** 2) * nvis)
+
+
+def test_dirty_pixels_direct_matches_fft_path():
+    """The per-pixel direct evaluation used for large spot checks equals the FFT path."""
+    n_img, N, W, Ms, nvis = 32, 64, 7, 1000, 300
+    T, x, hvec, uv = setup(n_img, N, W, Ms, 1, nvis)
+    vis = S.complex_normal(nvis, 9)
+    plan = I.Plan(uv[:, 0], uv[:, 1], W, N)
+    img = I.dirty_image(plan, T, Ms, 1, hvec, n_img, vis)
+    py, px = np.array([0, 5, 16, 31]), np.array([3, 16, 0, 31])
+    d = I.dirty_pixels_direct(plan, T, Ms, 1, hvec[px], hvec[py], vis, None, x[px], x[py])
+    np.testing.assert_allclose(d, img[py, px], atol=1e-12 * np.abs(img).max())
