@@ -1,0 +1,200 @@
+/*
+ * lmg.h -- C ABI of the least-misfit gridding library for GB300 (sm_103a).
+ *
+ * Method: Ye, Gull, Tan & Nikolic, "Optimal gridding and degridding in radio
+ * interferometry imaging", MNRAS 2019 (arXiv:1906.07102). Section and equation numbers
+ * below refer to that paper (equations numbered in order of appearance: Eq. 3 DFT dirty
+ * image, Eq. 4 FFT dirty image, Eq. 5 gridding sum, Eq. 6 support set, Eq. 8 misfit
+ * bound, Eq. 11 map error, Eq. 12/15 optimal correction, Eq. 16 integrated misfit,
+ * Eqs. 17-19 the linear system for C).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Visibility positions uv are float64 pairs (u, v) in wavelengths, array [nvis][2].
+ *    They are converted to grid cells by the float64 product u_cells = u * (N * pixel_scale)
+ *    (Section 2.1: u' = u L with the FFT field L = N * pixel_scale radians).
+ *  - x0 is the kept fraction of the FFT image width: the image has n_image pixels per
+ *    side and the grid N = n_image / x0 cells (N must be an even integer). The paper's
+ *    x0 (half width of the kept field in normalised coordinates) is x0 / 2.
+ *  - Grid arrays are [N][N] complex, row = v, column = u, index i = n + N/2 for the grid
+ *    coordinate n in [-N/2, N/2) (Eq. 4); support points outside wrap modulo N.
+ *  - Images are [n_image][n_image] complex, pixel p at x = (p - n_image/2) / N.
+ *  - Imaging uses exp(+i 2 pi n x) with no normalisation (Eqs. 3-4); prediction uses
+ *    exp(-i 2 pi (u l + v m)) (Eq. 2). Weights are real; NULL means all ones.
+ *  - dtype LMG_C64: complex64 data, float32 table and float32 arithmetic;
+ *    dtype LMG_C128: complex128 data, float64 table and float64 arithmetic.
+ *  - Complex arrays are interleaved (re, im) pairs, 8-byte (C64) or 16-byte (C128)
+ *    aligned. All data pointers are DEVICE pointers owned by the caller unless a
+ *    parameter says "host". The library owns only the opaque table and plan objects
+ *    (and the device buffers inside a plan); free them with lmg_*_free.
+ *  - stream is a cudaStream_t passed as void* (NULL = legacy default stream). Every call
+ *    that takes a stream only enqueues work and returns without synchronising, except
+ *    where a comment says otherwise.
+ *  - Positions that are not finite or lie 2^30 or more cells from the origin are dropped
+ *    (they contribute nothing when gridding and are predicted as 0); lmg_plan_dropped
+ *    reports how many were dropped by the last binning.
+ *  - The support rule (Eq. 6): a position u (cells) is quantised to 2^-32 cell (round
+ *    half to even) and covers the W grid points n_start .. n_start+W-1 with
+ *    n_start = ceil(u - W/2); its table coordinate is s = n_start - (u - W/2) in [0, 1).
+ *
+ * Errors: every function returns LMG_OK (0) or a negative lmg_status; no call throws or
+ * aborts. lmg_last_error() returns a message for the calling thread's last failure.
+ */
+#ifndef LMG_H
+#define LMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LMG_OK = 0,
+  LMG_EINVAL = -1,        /* invalid argument (range, null pointer, size) */
+  LMG_ENOMEM = -2,        /* host or device allocation failed */
+  LMG_ECUDA = -3,         /* a CUDA runtime call or kernel launch failed */
+  LMG_ECUFFT = -4,        /* a cuFFT call failed */
+  LMG_EUNSUPPORTED = -5,  /* valid request this build does not implement */
+  LMG_ENOCONV = -6        /* the least-misfit optimisation did not converge */
+} lmg_status;
+
+enum { LMG_C64 = 0, LMG_C128 = 1 };
+enum { LMG_INTERP_NEAREST = 0, LMG_INTERP_LINEAR = 1 };
+enum { LMG_CORR_HOPT = 0, LMG_CORR_INV_C = 1 };
+enum { LMG_ACCUM_PLAIN = 0, LMG_ACCUM_COMPENSATED = 1 };
+enum { LMG_CROP = 0, LMG_PAD = 1 };
+enum { LMG_FFT_IMAGE = +1, LMG_FFT_MODEL = -1 };
+
+typedef struct lmg_table lmg_table; /* least-misfit function (host float64) */
+typedef struct lmg_plan lmg_plan;   /* device state for one (table, n_image, x0, pixel_scale) */
+
+/* lmg_kernel_table -- build the least-misfit gridding function and its look-up table.
+ *
+ * Section 2.1 and Appendices A, B, E: h(x) is represented on Ng+1 = 33 nodes in
+ * [0, x0_paper] with h(0) = 1 and optimised by Levenberg-Marquardt to minimise the
+ * integrated map error E (Eq. 16), with C_r(s) solved per offset set from the normal
+ * equations (Eqs. 17-19, W <= 11) or by QR least squares (Appendix B, W > 11). Initial
+ * guesses: h = 1 for W <= 4, h_W = h_{W-1}^2 / h_{W-2} above (Appendix A). The table holds
+ * rows s_i = i / oversample, i = 0..oversample, of the W values C(j - W/2 + s_i)
+ * (Appendix E; one guard row at s = 1 so interpolation never crosses the odd-W jump of
+ * Appendix C). Host-only float64 work; no GPU is touched.
+ *
+ *   W          support width, 1..16
+ *   x0         kept fraction of the FFT image, 0 < x0 <= 1 (paper's x0 = x0 / 2)
+ *   oversample table sampling rate M_s per cell, 2..1000000
+ *   interp     LMG_INTERP_NEAREST or LMG_INTERP_LINEAR (Appendix F, d = 0 or 1)
+ *   correction LMG_CORR_HOPT (h = c / D, Eqs. 12, 15) or LMG_CORR_INV_C (h = 1/c)
+ *   out        receives the new table (caller frees with lmg_table_free)
+ * Returns LMG_EINVAL on a bad argument, LMG_ENOMEM, LMG_ENOCONV if the optimiser fails.
+ */
+int lmg_kernel_table(int W, double x0, int oversample, int interp, int correction,
+                     lmg_table** out);
+
+/* lmg_table_from_values -- a table from caller-supplied host values C[(oversample+1)][W]
+ * in the layout lmg_kernel_table builds (row i at s = i / oversample, entry j is
+ * C(j - W/2 + s)). Lets any separable gridding function be used with the same kernels.
+ * The values are copied. */
+int lmg_table_from_values(int W, double x0, int oversample, int interp, int correction,
+                          const double* C_host, lmg_table** out);
+
+int lmg_table_free(lmg_table* t);
+
+/* lmg_table_export -- copy host float64 data out of a table (any pointer may be NULL).
+ *   C_host   [(oversample+1)][W] table values, nC = capacity in doubles
+ *   h_host   [Ng+1] node values of h on [0, x0_paper] (all zero for a caller table),
+ *            nh = capacity in doubles
+ *   E        integrated misfit E at the optimum (Eq. 16; NaN for a caller table)
+ *   info     [4] ints: W, oversample, Ng, iterations of the optimiser */
+int lmg_table_export(const lmg_table* t, double* C_host, size_t nC, double* h_host,
+                     size_t nh, double* E, int* info);
+
+/* lmg_correction_export -- the grid-correction factors h(x_p) (host float64) at the
+ * n_image kept pixels x_p = (p - n_image/2) / N, N = n_image / x0, for the table function
+ * actually used (c and D integrated over s with 8-point Gauss-Legendre per table piece;
+ * Eqs. 12-15). If single_precision is nonzero the table values are first rounded to
+ * float32, as the LMG_C64 path uses them. h_host has n_image doubles. */
+int lmg_correction_export(const lmg_table* t, int64_t n_image, int single_precision,
+                          double* h_host);
+
+/* lmg_plan_create -- device state for imaging with one table at one image size.
+ *   n_image      kept image side (pixels); N = n_image / x0 must be an even integer,
+ *                a multiple of 32, and at least 64
+ *   pixel_scale  image pixel size in radians (u_cells = u * N * pixel_scale)
+ *   max_vis      capacity: the largest nvis later passed to lmg_plan_bin (>= 1)
+ *   dtype        LMG_C64 or LMG_C128
+ * Allocates the device table, correction factors, binning buffers sized for max_vis, a
+ * work grid [N][N] and a cuFFT plan; uses the current CUDA device. Synchronous.
+ * Returns LMG_EINVAL, LMG_ENOMEM, LMG_ECUDA or LMG_ECUFFT on failure. */
+int lmg_plan_create(const lmg_table* t, int64_t n_image, double pixel_scale,
+                    int64_t max_vis, int dtype, lmg_plan** out);
+int lmg_plan_free(lmg_plan* p);
+
+/* lmg_plan_bin -- bin visibility positions for gridding and degridding (support rule of
+ * Eq. 6; sort into 32-column strips by support-start row; balanced work items). Must be
+ * called before lmg_grid / lmg_degrid / lmg_dirty_image / lmg_predict_vis and again
+ * whenever the positions change. uv: device float64 [nvis][2] in wavelengths,
+ * 0 <= nvis <= max_vis. Allocates nothing. */
+int lmg_plan_bin(lmg_plan* p, const double* uv, int64_t nvis, void* stream);
+
+/* lmg_plan_dropped -- number of positions dropped by the last lmg_plan_bin (not finite
+ * or 2^30 cells or more from the origin). Synchronises the given stream. */
+int lmg_plan_dropped(lmg_plan* p, int64_t* dropped, void* stream);
+
+/* lmg_grid -- G_n = sum_k w_k V_k C(n - u_k) C(m - v_k) over each support (Eqs. 5-6).
+ *   vis      device complex [nvis] of the plan's dtype
+ *   weights  device real [nvis] (float for C64, double for C128) or NULL (all ones)
+ *   accum    LMG_ACCUM_PLAIN, or LMG_ACCUM_COMPENSATED (C64 only: each accumulator is
+ *            a float pair updated with an error-free sum)
+ *   grid     device complex [N][N]; every cell is overwritten (no pre-zeroing needed)
+ * Allocates nothing. */
+int lmg_grid(lmg_plan* p, const void* vis, const void* weights, int accum, void* grid,
+             void* stream);
+
+/* lmg_degrid -- V_k = sum_{i,j} C(n_i - u_k) C(m_j - v_k) G[m_j][n_i] (Section 4, the
+ * transpose of lmg_grid without weights). grid: device complex [N][N];
+ * vis_out: device complex [nvis], every entry overwritten. Allocates nothing. */
+int lmg_degrid(lmg_plan* p, const void* grid, void* vis_out, void* stream);
+
+/* lmg_fft -- unnormalised in-place 2-D FFT of a device grid [N][N] in grid index order.
+ * direction LMG_FFT_IMAGE computes sum_i G[i] exp(+i 2 pi i q / N) (cuFFT inverse);
+ * LMG_FFT_MODEL computes sum_q P[q] exp(-i 2 pi i q / N) (cuFFT forward). */
+int lmg_fft(lmg_plan* p, int direction, void* grid, void* stream);
+
+/* lmg_grid_correct -- grid correction and crop (Eqs. 4, 15), or its adjoint.
+ *   LMG_CROP: in = FFT output [N][N] of a grid in index order, out = image
+ *             [n_image][n_image] with out[p][q] = h(y_p) h(x_q) F(x_q, y_p).
+ *   LMG_PAD:  in = image [n_image][n_image], out = [N][N] array that LMG_FFT_MODEL turns
+ *             into the model grid in index order (zero outside the kept pixels).
+ * Allocates nothing. */
+int lmg_grid_correct(lmg_plan* p, int direction, const void* in, void* out, void* stream);
+
+/* lmg_dirty_image -- grid, FFT (+i), correct and crop into image_out [n_image][n_image],
+ * using the plan's work grid. Allocates nothing. */
+int lmg_dirty_image(lmg_plan* p, const void* vis, const void* weights, int accum,
+                    void* image_out, void* stream);
+
+/* lmg_predict_vis -- pad and correct image [n_image][n_image], FFT (-i), degrid into
+ * vis_out [nvis], using the plan's work grid. Allocates nothing. */
+int lmg_predict_vis(lmg_plan* p, const void* image, void* vis_out, void* stream);
+
+/* lmg_plan_info -- sizes of a plan: out[0] = N, out[1] = n_image, out[2] = W,
+ * out[3] = nvis of the last binning, out[4] = records, out[5] = work items (records and
+ * items need a synchronised stream to be current), out[6] = dtype. */
+int lmg_plan_info(lmg_plan* p, int64_t* out, void* stream);
+
+/* lmg_work_grid -- device pointer of the plan's internal [N][N] work grid (valid until
+ * lmg_plan_free); holds the FFT-domain grid after lmg_dirty_image / lmg_predict_vis. */
+void* lmg_work_grid(lmg_plan* p);
+
+/* lmg_last_error -- message for the calling thread's most recent failure ("" if none). */
+const char* lmg_last_error(void);
+
+/* lmg_version -- library version string. */
+const char* lmg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LMG_H */

@@ -1,0 +1,531 @@
+// C ABI of liblmg (include/lmg.h): argument checking, plan state, cuFFT and the launch
+// sequences of lmg_dirty_image / lmg_predict_vis.
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "device_common.cuh"
+#include "kernels.h"
+#include "lmg_internal.h"
+
+namespace lmg {
+namespace {
+thread_local std::string g_error;
+}
+int set_error(int status, const std::string& msg) {
+  g_error = msg;
+  return status;
+}
+void clear_error() { g_error.clear(); }
+}  // namespace lmg
+
+using namespace lmg;
+
+struct lmg_plan {
+  int W = 0, Ms = 0, interp = 1, dtype = 0, Wp = 0;
+  int64_t n_image = 0, N = 0;
+  double x0 = 0, pixel_scale = 0, scale2 = 0;
+  int n_strips = 0, rows_per_block = 256, item_target = 1024, item_cap = 0, nchunks = 0;
+  int64_t max_vis = 0, nvis = -1;
+  int device = 0, sms = 0;
+  int blocks_grid = 0, blocks_degrid = 0;
+  bool tab_smem = false;
+  size_t smem_grid = 0, smem_degrid = 0, smem_grid_comp = 0;
+  int blocks_grid_comp = 0;
+  void* d_table = nullptr;
+  void* d_h = nullptr;
+  VisPos* pos = nullptr;
+  int* hist = nullptr;
+  int* offsets = nullptr;
+  int* cursor = nullptr;
+  int* partial = nullptr;
+  Rec* recs = nullptr;
+  int* dup_list = nullptr;
+  int* bad_list = nullptr;
+  Item* items = nullptr;
+  int* counters = nullptr;
+  void* spill = nullptr;
+  void* dpart = nullptr;
+  void* work = nullptr;
+  cufftHandle fft = 0;
+  bool fft_ok = false;
+};
+
+namespace {
+
+const char* kVersion = "lmg 0.1 (sm_103a)";
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return set_error(LMG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+bool check_table_args(int W, double x0, int Ms, int interp, int correction) {
+  if (W < 1 || W > kMaxW) return set_error(LMG_EINVAL, "W must be in [1, 16]"), false;
+  if (!(x0 > 0.0 && x0 <= 1.0)) return set_error(LMG_EINVAL, "x0 must be in (0, 1]"), false;
+  if (Ms < 2 || Ms > 1000000) return set_error(LMG_EINVAL, "oversample must be in [2, 1000000]"), false;
+  if (interp != LMG_INTERP_NEAREST && interp != LMG_INTERP_LINEAR)
+    return set_error(LMG_EINVAL, "interp must be LMG_INTERP_NEAREST or LMG_INTERP_LINEAR"), false;
+  if (correction != LMG_CORR_HOPT && correction != LMG_CORR_INV_C)
+    return set_error(LMG_EINVAL, "correction must be LMG_CORR_HOPT or LMG_CORR_INV_C"), false;
+  return true;
+}
+
+template <typename T> int dalloc(T** p, size_t count, const char* what) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * count);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return set_error(e == cudaErrorMemoryAllocation ? LMG_ENOMEM : LMG_ECUDA,
+                     std::string("device allocation of ") + what + " failed: " + cudaGetErrorString(e));
+  }
+  return LMG_OK;
+}
+
+void free_plan(lmg_plan* p) {
+  if (!p) return;
+  void* ptrs[] = {p->d_table, p->d_h, p->pos, p->hist, p->offsets, p->cursor, p->partial, p->recs,
+                  p->dup_list, p->bad_list, p->items, p->counters, p->spill, p->dpart, p->work};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  if (p->fft_ok) cufftDestroy(p->fft);
+  delete p;
+}
+
+SweepArgs sweep_args(const lmg_plan* p) {
+  SweepArgs a{};
+  a.recs = p->recs;
+  a.offsets = p->offsets;
+  a.items = p->items;
+  a.counters = p->counters;
+  a.table = p->d_table;
+  a.Wp = p->Wp;
+  a.Ms = p->Ms;
+  a.interp = p->interp;
+  a.N = static_cast<int>(p->N);
+  a.n_strips = p->n_strips;
+  a.W = p->W;
+  a.dtype = p->dtype;
+  a.item_cap = p->item_cap;
+  a.table_in_smem = p->tab_smem ? 1 : 0;
+  a.dup_list = p->dup_list;
+  a.bad_list = p->bad_list;
+  a.nvis = p->nvis;
+  return a;
+}
+
+int need_binned(const lmg_plan* p) {
+  if (p->nvis < 0) return set_error(LMG_EINVAL, "plan has no binned positions (call lmg_plan_bin first)");
+  return LMG_OK;
+}
+
+int launch_status(int rc, const char* what) {
+  if (rc != 0) {
+    cudaError_t e = cudaGetLastError();
+    return set_error(LMG_ECUDA, std::string(what) + " launch failed: " + cudaGetErrorString(e));
+  }
+  return LMG_OK;
+}
+
+int do_grid(lmg_plan* p, const void* vis, const void* weights, int accum, void* grid, cudaStream_t st) {
+  SweepArgs a = sweep_args(p);
+  a.accum = accum;
+  a.vis = vis;
+  a.weights = weights;
+  a.grid = grid;
+  a.spill = p->spill;
+  a.grid_blocks = accum ? p->blocks_grid_comp : p->blocks_grid;
+  return launch_status(grid_launch(a, st), "gridding");
+}
+
+int do_degrid(lmg_plan* p, const void* grid, void* vis_out, cudaStream_t st) {
+  SweepArgs a = sweep_args(p);
+  a.grid_in = grid;
+  a.vis_out = vis_out;
+  a.dpart = p->dpart;
+  a.grid_blocks = p->blocks_degrid;
+  return launch_status(degrid_launch(a, st), "degridding");
+}
+
+int do_fft(lmg_plan* p, int direction, void* g, cudaStream_t st) {
+  if (cufftSetStream(p->fft, st) != CUFFT_SUCCESS) return set_error(LMG_ECUFFT, "cufftSetStream failed");
+  cufftResult r;
+  const int dir = direction == LMG_FFT_IMAGE ? CUFFT_INVERSE : CUFFT_FORWARD;
+  if (p->dtype == LMG_C128)
+    r = cufftExecZ2Z(p->fft, static_cast<cufftDoubleComplex*>(g), static_cast<cufftDoubleComplex*>(g), dir);
+  else
+    r = cufftExecC2C(p->fft, static_cast<cufftComplex*>(g), static_cast<cufftComplex*>(g), dir);
+  if (r != CUFFT_SUCCESS) return set_error(LMG_ECUFFT, "cuFFT execution failed (code " + std::to_string(int(r)) + ")");
+  return LMG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lmg_last_error(void) { return g_error.c_str(); }
+const char* lmg_version(void) { return kVersion; }
+
+int lmg_kernel_table(int W, double x0, int oversample, int interp, int correction, lmg_table** out) {
+  clear_error();
+  if (!out) return set_error(LMG_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!check_table_args(W, x0, oversample, interp, correction)) return LMG_EINVAL;
+  lmg_table* t = new (std::nothrow) lmg_table;
+  if (!t) return set_error(LMG_ENOMEM, "host allocation failed");
+  t->W = W;
+  t->x0 = x0;
+  t->x0p = 0.5 * x0;
+  t->Ms = oversample;
+  t->interp = interp;
+  t->correction = correction;
+  int rc;
+  try {
+    rc = build_least_misfit(W, t->x0p, oversample, t);
+  } catch (const std::bad_alloc&) {
+    rc = set_error(LMG_ENOMEM, "host allocation failed");
+  }
+  if (rc != LMG_OK) {
+    delete t;
+    return rc;
+  }
+  *out = t;
+  return LMG_OK;
+}
+
+int lmg_table_from_values(int W, double x0, int oversample, int interp, int correction, const double* C_host,
+                          lmg_table** out) {
+  clear_error();
+  if (!out) return set_error(LMG_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!C_host) return set_error(LMG_EINVAL, "C_host is NULL");
+  if (!check_table_args(W, x0, oversample, interp, correction)) return LMG_EINVAL;
+  lmg_table* t = new (std::nothrow) lmg_table;
+  if (!t) return set_error(LMG_ENOMEM, "host allocation failed");
+  t->W = W;
+  t->x0 = x0;
+  t->x0p = 0.5 * x0;
+  t->Ms = oversample;
+  t->interp = interp;
+  t->correction = correction;
+  t->E = std::nan("");
+  t->h_nodes.assign(kNg + 1, 0.0);
+  try {
+    t->C.assign(C_host, C_host + size_t(oversample + 1) * W);
+  } catch (const std::bad_alloc&) {
+    delete t;
+    return set_error(LMG_ENOMEM, "host allocation failed");
+  }
+  for (double v : t->C)
+    if (!std::isfinite(v)) {
+      delete t;
+      return set_error(LMG_EINVAL, "table values must be finite");
+    }
+  *out = t;
+  return LMG_OK;
+}
+
+int lmg_table_free(lmg_table* t) {
+  delete t;
+  return LMG_OK;
+}
+
+int lmg_table_export(const lmg_table* t, double* C_host, size_t nC, double* h_host, size_t nh, double* E,
+                     int* info) {
+  clear_error();
+  if (!t) return set_error(LMG_EINVAL, "table is NULL");
+  if (C_host) {
+    if (nC < t->C.size()) return set_error(LMG_EINVAL, "C_host capacity too small");
+    std::memcpy(C_host, t->C.data(), sizeof(double) * t->C.size());
+  }
+  if (h_host) {
+    if (nh < t->h_nodes.size()) return set_error(LMG_EINVAL, "h_host capacity too small");
+    std::memcpy(h_host, t->h_nodes.data(), sizeof(double) * t->h_nodes.size());
+  }
+  if (E) *E = t->E;
+  if (info) {
+    info[0] = t->W;
+    info[1] = t->Ms;
+    info[2] = kNg;
+    info[3] = t->iterations;
+  }
+  return LMG_OK;
+}
+
+int lmg_correction_export(const lmg_table* t, int64_t n_image, int single_precision, double* h_host) {
+  clear_error();
+  if (!t || !h_host) return set_error(LMG_EINVAL, "NULL argument");
+  if (n_image < 2 || (n_image & 1)) return set_error(LMG_EINVAL, "n_image must be even and >= 2");
+  const double Nd = double(n_image) / t->x0;
+  const int64_t N = int64_t(std::llround(Nd));
+  if (std::fabs(Nd - double(N)) > 1e-9 * Nd || (N & 1))
+    return set_error(LMG_EINVAL, "n_image / x0 must be an even integer");
+  correction_factors(t, n_image, N, single_precision != 0, h_host);
+  return LMG_OK;
+}
+
+int lmg_plan_create(const lmg_table* t, int64_t n_image, double pixel_scale, int64_t max_vis, int dtype,
+                    lmg_plan** out) {
+  clear_error();
+  if (!out) return set_error(LMG_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!t) return set_error(LMG_EINVAL, "table is NULL");
+  if (dtype != LMG_C64 && dtype != LMG_C128) return set_error(LMG_EINVAL, "dtype must be LMG_C64 or LMG_C128");
+  if (!(pixel_scale > 0.0) || !std::isfinite(pixel_scale)) return set_error(LMG_EINVAL, "pixel_scale must be > 0");
+  if (max_vis < 1 || max_vis > (int64_t(1) << 30)) return set_error(LMG_EINVAL, "max_vis must be in [1, 2^30]");
+  if (n_image < 2 || (n_image & 1)) return set_error(LMG_EINVAL, "n_image must be even and >= 2");
+  const double Nd = double(n_image) / t->x0;
+  const int64_t N = int64_t(std::llround(Nd));
+  if (std::fabs(Nd - double(N)) > 1e-9 * Nd || (N & 1))
+    return set_error(LMG_EINVAL, "n_image / x0 must be an even integer");
+  if (N < 64 || N % kStrip != 0 || N > 65536)
+    return set_error(LMG_EINVAL, "grid size N = n_image / x0 must be a multiple of 32 in [64, 65536]");
+  if (N < 2 * t->W) return set_error(LMG_EINVAL, "grid too small for the support width");
+
+  lmg_plan* p = new (std::nothrow) lmg_plan;
+  if (!p) return set_error(LMG_ENOMEM, "host allocation failed");
+  p->W = t->W;
+  p->Ms = t->Ms;
+  p->interp = t->interp;
+  p->dtype = dtype;
+  p->n_image = n_image;
+  p->N = N;
+  p->x0 = t->x0;
+  p->pixel_scale = pixel_scale;
+  p->scale2 = double(N) * pixel_scale * 4294967296.0;
+  p->max_vis = max_vis;
+  p->n_strips = int(N / kStrip);
+  const size_t rs = dtype == LMG_C128 ? 8 : 4;
+  p->Wp = dtype == LMG_C128 ? ((p->W + 1) & ~1) : ((p->W + 3) & ~3);
+  const int nblk = int((N + p->rows_per_block - 1) / p->rows_per_block);
+  p->item_cap = p->n_strips * nblk + int((2 * max_vis) / p->item_target) + 2;
+  const long long L = (long long)p->n_strips * N;
+  p->nchunks = bin_scan_chunks(L);
+
+  int rc;
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e != cudaSuccess) {
+    delete p;
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
+  if (e != cudaSuccess) {
+    delete p;
+    return cuda_fail(e, "cudaDeviceGetAttribute");
+  }
+  // Device table (rows padded to Wp) and correction factors in the plan's precision.
+  std::vector<double> hcorr(static_cast<size_t>(n_image));
+  correction_factors(t, n_image, N, dtype == LMG_C64, hcorr.data());
+  std::vector<unsigned char> tab_bytes(size_t(p->Ms + 1) * p->Wp * rs, 0), h_bytes(size_t(n_image) * rs);
+  for (int i = 0; i <= p->Ms; ++i)
+    for (int j = 0; j < p->W; ++j) {
+      const double v = t->C[size_t(i) * p->W + j];
+      if (rs == 8) reinterpret_cast<double*>(tab_bytes.data())[size_t(i) * p->Wp + j] = v;
+      else reinterpret_cast<float*>(tab_bytes.data())[size_t(i) * p->Wp + j] = float(v);
+    }
+  for (int64_t q = 0; q < n_image; ++q) {
+    if (rs == 8) reinterpret_cast<double*>(h_bytes.data())[q] = hcorr[size_t(q)];
+    else reinterpret_cast<float*>(h_bytes.data())[q] = float(hcorr[size_t(q)]);
+  }
+  const size_t c2 = 2 * rs;
+  if ((rc = dalloc(reinterpret_cast<unsigned char**>(&p->d_table), tab_bytes.size(), "table")) ||
+      (rc = dalloc(reinterpret_cast<unsigned char**>(&p->d_h), h_bytes.size(), "correction")) ||
+      (rc = dalloc(&p->pos, size_t(max_vis), "positions")) || (rc = dalloc(&p->hist, size_t(L), "histogram")) ||
+      (rc = dalloc(&p->offsets, size_t(L) + 1, "offsets")) || (rc = dalloc(&p->cursor, size_t(L), "cursor")) ||
+      (rc = dalloc(&p->partial, size_t(p->nchunks), "scan")) || (rc = dalloc(&p->recs, size_t(2 * max_vis), "records")) ||
+      (rc = dalloc(&p->dup_list, size_t(max_vis), "dup list")) ||
+      (rc = dalloc(&p->bad_list, size_t(max_vis), "dropped list")) ||
+      (rc = dalloc(&p->items, size_t(p->item_cap), "items")) || (rc = dalloc(&p->counters, 8, "counters")) ||
+      (rc = dalloc(reinterpret_cast<unsigned char**>(&p->spill), size_t(p->item_cap) * p->W * kStrip * c2, "spill")) ||
+      (rc = dalloc(reinterpret_cast<unsigned char**>(&p->dpart), size_t(max_vis) * c2, "partials")) ||
+      (rc = dalloc(reinterpret_cast<unsigned char**>(&p->work), size_t(N) * size_t(N) * c2, "work grid"))) {
+    free_plan(p);
+    return rc;
+  }
+  if ((e = cudaMemcpy(p->d_table, tab_bytes.data(), tab_bytes.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(p->d_h, h_bytes.data(), h_bytes.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemset(p->counters, 0, 8 * sizeof(int))) != cudaSuccess) {
+    free_plan(p);
+    return cuda_fail(e, "plan upload");
+  }
+  // Launch shapes: table in shared memory when it is small; persistent CTAs per SM.
+  p->tab_smem = tab_bytes.size() <= 64 * 1024;
+  p->smem_grid = sweep_smem_bytes(p->W, dtype, p->Ms, p->tab_smem, false);
+  p->smem_degrid = sweep_smem_bytes(p->W, dtype, p->Ms, p->tab_smem, true);
+  int bps = 0;
+  if (sweep_set_smem_limits(p->W, dtype, 0, p->smem_grid, false) ||
+      sweep_set_smem_limits(p->W, dtype, 0, p->smem_degrid, true) ||
+      sweep_occupancy(p->W, dtype, 0, p->smem_grid, false, &bps)) {
+    free_plan(p);
+    return cuda_fail(cudaGetLastError(), "sweep kernel attributes");
+  }
+  p->blocks_grid = p->sms * (bps > 0 ? bps : 1);
+  if (sweep_occupancy(p->W, dtype, 0, p->smem_degrid, true, &bps)) {
+    free_plan(p);
+    return cuda_fail(cudaGetLastError(), "sweep kernel attributes");
+  }
+  p->blocks_degrid = p->sms * (bps > 0 ? bps : 1);
+  if (dtype == LMG_C64) {
+    if (sweep_set_smem_limits(p->W, dtype, 1, p->smem_grid, false) ||
+        sweep_occupancy(p->W, dtype, 1, p->smem_grid, false, &bps)) {
+      free_plan(p);
+      return cuda_fail(cudaGetLastError(), "sweep kernel attributes");
+    }
+    p->blocks_grid_comp = p->sms * (bps > 0 ? bps : 1);
+  }
+  const cufftResult fr = cufftPlan2d(&p->fft, int(N), int(N), dtype == LMG_C128 ? CUFFT_Z2Z : CUFFT_C2C);
+  if (fr != CUFFT_SUCCESS) {
+    free_plan(p);
+    return set_error(fr == CUFFT_ALLOC_FAILED ? LMG_ENOMEM : LMG_ECUFFT,
+                     "cufftPlan2d failed (code " + std::to_string(int(fr)) + ")");
+  }
+  p->fft_ok = true;
+  *out = p;
+  return LMG_OK;
+}
+
+int lmg_plan_free(lmg_plan* p) {
+  free_plan(p);
+  return LMG_OK;
+}
+
+int lmg_plan_bin(lmg_plan* p, const double* uv, int64_t nvis, void* stream) {
+  clear_error();
+  if (!p) return set_error(LMG_EINVAL, "plan is NULL");
+  if (nvis < 0 || nvis > p->max_vis) return set_error(LMG_EINVAL, "nvis must be in [0, max_vis]");
+  if (nvis > 0 && !uv) return set_error(LMG_EINVAL, "uv is NULL");
+  if (reinterpret_cast<uintptr_t>(uv) % 16 != 0) return set_error(LMG_EINVAL, "uv must be 16-byte aligned");
+  BinArgs a{};
+  a.uv = uv;
+  a.nvis = nvis;
+  a.scale2 = p->scale2;
+  a.W = p->W;
+  a.N = int(p->N);
+  a.n_strips = p->n_strips;
+  a.rows_per_block = p->rows_per_block;
+  a.item_target = p->item_target;
+  a.item_cap = p->item_cap;
+  a.max_blocks = p->sms * 8;
+  a.pos = p->pos;
+  a.hist = p->hist;
+  a.offsets = p->offsets;
+  a.cursor = p->cursor;
+  a.partial = p->partial;
+  a.recs = p->recs;
+  a.dup_list = p->dup_list;
+  a.bad_list = p->bad_list;
+  a.items = p->items;
+  a.counters = p->counters;
+  const int rc = launch_status(bin_launch(a, static_cast<cudaStream_t>(stream)), "binning");
+  if (rc == LMG_OK) p->nvis = nvis;
+  return rc;
+}
+
+int lmg_plan_dropped(lmg_plan* p, int64_t* dropped, void* stream) {
+  clear_error();
+  if (!p || !dropped) return set_error(LMG_EINVAL, "NULL argument");
+  int c[8];
+  cudaError_t e = cudaMemcpyAsync(c, p->counters, sizeof(c), cudaMemcpyDeviceToHost, static_cast<cudaStream_t>(stream));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "reading counters");
+  *dropped = c[kCntBad];
+  return LMG_OK;
+}
+
+int lmg_plan_info(lmg_plan* p, int64_t* out, void* stream) {
+  clear_error();
+  if (!p || !out) return set_error(LMG_EINVAL, "NULL argument");
+  int c[8];
+  cudaError_t e = cudaMemcpyAsync(c, p->counters, sizeof(c), cudaMemcpyDeviceToHost, static_cast<cudaStream_t>(stream));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "reading counters");
+  int total = 0;
+  if (p->nvis >= 0) {
+    e = cudaMemcpy(&total, p->offsets + (long long)p->n_strips * p->N, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "reading offsets");
+  }
+  out[0] = p->N;
+  out[1] = p->n_image;
+  out[2] = p->W;
+  out[3] = p->nvis;
+  out[4] = total;
+  out[5] = c[kCntItems];
+  out[6] = p->dtype;
+  return LMG_OK;
+}
+
+void* lmg_work_grid(lmg_plan* p) { return p ? p->work : nullptr; }
+
+int lmg_grid(lmg_plan* p, const void* vis, const void* weights, int accum, void* grid, void* stream) {
+  clear_error();
+  if (!p || !grid) return set_error(LMG_EINVAL, "NULL argument");
+  if (int rc = need_binned(p)) return rc;
+  if (p->nvis > 0 && !vis) return set_error(LMG_EINVAL, "vis is NULL");
+  if (accum != LMG_ACCUM_PLAIN && accum != LMG_ACCUM_COMPENSATED) return set_error(LMG_EINVAL, "bad accum");
+  if (accum == LMG_ACCUM_COMPENSATED && p->dtype != LMG_C64)
+    return set_error(LMG_EUNSUPPORTED, "compensated accumulation is for LMG_C64");
+  return do_grid(p, vis, weights, accum, grid, static_cast<cudaStream_t>(stream));
+}
+
+int lmg_degrid(lmg_plan* p, const void* grid, void* vis_out, void* stream) {
+  clear_error();
+  if (!p || !grid) return set_error(LMG_EINVAL, "NULL argument");
+  if (int rc = need_binned(p)) return rc;
+  if (p->nvis > 0 && !vis_out) return set_error(LMG_EINVAL, "vis_out is NULL");
+  return do_degrid(p, grid, vis_out, static_cast<cudaStream_t>(stream));
+}
+
+int lmg_fft(lmg_plan* p, int direction, void* grid, void* stream) {
+  clear_error();
+  if (!p || !grid) return set_error(LMG_EINVAL, "NULL argument");
+  if (direction != LMG_FFT_IMAGE && direction != LMG_FFT_MODEL) return set_error(LMG_EINVAL, "bad direction");
+  return do_fft(p, direction, grid, static_cast<cudaStream_t>(stream));
+}
+
+int lmg_grid_correct(lmg_plan* p, int direction, const void* in, void* out, void* stream) {
+  clear_error();
+  if (!p || !in || !out) return set_error(LMG_EINVAL, "NULL argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc;
+  if (direction == LMG_CROP) rc = crop_correct_launch(in, out, p->d_h, int(p->n_image), int(p->N), p->dtype, st);
+  else if (direction == LMG_PAD) rc = pad_correct_launch(in, out, p->d_h, int(p->n_image), int(p->N), p->dtype, st);
+  else return set_error(LMG_EINVAL, "direction must be LMG_CROP or LMG_PAD");
+  return launch_status(rc, "grid correction");
+}
+
+int lmg_dirty_image(lmg_plan* p, const void* vis, const void* weights, int accum, void* image_out, void* stream) {
+  clear_error();
+  if (!p || !image_out) return set_error(LMG_EINVAL, "NULL argument");
+  if (int rc = need_binned(p)) return rc;
+  if (p->nvis > 0 && !vis) return set_error(LMG_EINVAL, "vis is NULL");
+  if (accum != LMG_ACCUM_PLAIN && accum != LMG_ACCUM_COMPENSATED) return set_error(LMG_EINVAL, "bad accum");
+  if (accum == LMG_ACCUM_COMPENSATED && p->dtype != LMG_C64)
+    return set_error(LMG_EUNSUPPORTED, "compensated accumulation is for LMG_C64");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = do_grid(p, vis, weights, accum, p->work, st);
+  if (rc == LMG_OK) rc = do_fft(p, LMG_FFT_IMAGE, p->work, st);
+  if (rc == LMG_OK)
+    rc = launch_status(crop_correct_launch(p->work, image_out, p->d_h, int(p->n_image), int(p->N), p->dtype, st),
+                       "crop");
+  return rc;
+}
+
+int lmg_predict_vis(lmg_plan* p, const void* image, void* vis_out, void* stream) {
+  clear_error();
+  if (!p || !image) return set_error(LMG_EINVAL, "NULL argument");
+  if (int rc = need_binned(p)) return rc;
+  if (p->nvis > 0 && !vis_out) return set_error(LMG_EINVAL, "vis_out is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = launch_status(pad_correct_launch(image, p->work, p->d_h, int(p->n_image), int(p->N), p->dtype, st), "pad");
+  if (rc == LMG_OK) rc = do_fft(p, LMG_FFT_MODEL, p->work, st);
+  if (rc == LMG_OK) rc = do_degrid(p, p->work, vis_out, st);
+  return rc;
+}
+
+}  // extern "C"

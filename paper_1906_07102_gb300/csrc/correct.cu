@@ -1,0 +1,78 @@
+// Grid correction with crop (Eqs. 4, 15) and its adjoint, pad with correction.
+//
+// The grids are held in index order i = n + N/2. An unnormalised FFT of that array gives
+// sum_i G[i] e^{+i 2 pi i q / N} = (-1)^q sum_n G_n e^{+i 2 pi n q / N}, so the centring
+// shift is the checkerboard (-1)^(qx + qy) applied here, with q = p - n_image/2 the pixel
+// offset from the image centre (stored at q mod N).
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+#include "kernels.h"
+
+namespace lmg {
+namespace {
+
+template <typename R>
+__global__ void k_crop_correct(const typename Cplx<R>::T* __restrict__ F, typename Cplx<R>::T* __restrict__ img,
+                               const R* __restrict__ h, int n_img, int N) {
+  const int px = blockIdx.x * blockDim.x + threadIdx.x;
+  const int py = blockIdx.y;
+  if (px >= n_img) return;
+  const int qx = px - n_img / 2, qy = py - n_img / 2;
+  const int sx = qx < 0 ? qx + N : qx, sy = qy < 0 ? qy + N : qy;
+  const auto v = F[static_cast<size_t>(sy) * N + sx];
+  R f = h[px] * h[py];
+  if ((qx + qy) & 1) f = -f;
+  typename Cplx<R>::T o;
+  o.x = f * v.x;
+  o.y = f * v.y;
+  img[static_cast<size_t>(py) * n_img + px] = o;
+}
+
+template <typename R>
+__global__ void k_pad_correct(const typename Cplx<R>::T* __restrict__ img, typename Cplx<R>::T* __restrict__ P,
+                              const R* __restrict__ h, int n_img, int N) {
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+  const int iy = blockIdx.y;
+  if (ix >= N) return;
+  const int qx = ix < N / 2 ? ix : ix - N, qy = iy < N / 2 ? iy : iy - N;
+  typename Cplx<R>::T o;
+  o.x = 0;
+  o.y = 0;
+  const int half = n_img / 2;
+  if (qx >= -half && qx < n_img - half && qy >= -half && qy < n_img - half) {
+    const int px = qx + half, py = qy + half;
+    const auto v = img[static_cast<size_t>(py) * n_img + px];
+    R f = h[px] * h[py];
+    if ((qx + qy) & 1) f = -f;
+    o.x = f * v.x;
+    o.y = f * v.y;
+  }
+  P[static_cast<size_t>(iy) * N + ix] = o;
+}
+
+}  // namespace
+
+int crop_correct_launch(const void* F, void* img, const void* h, int n_img, int N, int dtype, cudaStream_t st) {
+  dim3 block(256), grid((n_img + 255) / 256, n_img);
+  if (dtype)
+    k_crop_correct<double><<<grid, block, 0, st>>>(static_cast<const double2*>(F), static_cast<double2*>(img),
+                                                   static_cast<const double*>(h), n_img, N);
+  else
+    k_crop_correct<float><<<grid, block, 0, st>>>(static_cast<const float2*>(F), static_cast<float2*>(img),
+                                                  static_cast<const float*>(h), n_img, N);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int pad_correct_launch(const void* img, void* P, const void* h, int n_img, int N, int dtype, cudaStream_t st) {
+  dim3 block(256), grid((N + 255) / 256, N);
+  if (dtype)
+    k_pad_correct<double><<<grid, block, 0, st>>>(static_cast<const double2*>(img), static_cast<double2*>(P),
+                                                  static_cast<const double*>(h), n_img, N);
+  else
+    k_pad_correct<float><<<grid, block, 0, st>>>(static_cast<const float2*>(img), static_cast<float2*>(P),
+                                                 static_cast<const float*>(h), n_img, N);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace lmg

@@ -1,0 +1,133 @@
+// Device-side types and helpers shared by the binning, gridding and degridding kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lmg {
+
+// Strip width: one warp lane per grid column.
+constexpr int kStrip = 32;
+constexpr int kFracBits = 32;
+
+// Support start (grid indices, wrapped to [0, N)) and fixed-point table coordinate of
+// one visibility; x0 < 0 marks a dropped position.
+struct VisPos {
+  int x0, y0;
+  unsigned su, sv;
+};
+
+// One binned record: a visibility as seen from one 32-column strip. xrel is the support
+// start column relative to the strip's first column (negative when the support started
+// in the previous strip, i.e. for the strip's secondary copy).
+struct Rec {
+  unsigned idx;
+  int xrel;
+  unsigned su, sv;
+};
+
+// Work item: rows [r0, r1) of one strip.
+struct Item {
+  int strip, r0, r1, pad;
+};
+
+template <typename R> struct Cplx;
+template <> struct Cplx<float> { using T = float2; };
+template <> struct Cplx<double> { using T = double2; };
+
+// Fixed point of the float64 product u * scale2, with scale2 = N * pixel_scale * 2^32:
+// U = round-half-even(fl64(u * scale2)) computed exactly with integer operations.
+// Returns false when the product is not finite or |U| >= 2^62 (|u_cells| >= 2^30).
+__device__ __forceinline__ bool fixed_position(double u, double scale2, long long& U) {
+  const double p = __dmul_rn(u, scale2);
+  const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(p));
+  const int e = int((bits >> 52) & 0x7ff);
+  if (e >= 1023 + 62) return false;  // too large, infinite or NaN
+  const bool neg = (bits >> 63) != 0;
+  unsigned long long q;
+  if (e == 0) {
+    q = 0;  // zero or subnormal: rounds to 0
+  } else {
+    const unsigned long long m = (bits & 0xfffffffffffffull) | (1ull << 52);
+    const int sh = e - 1075;
+    if (sh >= 0) {
+      q = m << sh;
+    } else {
+      const int k = -sh;
+      if (k > 54) {
+        q = 0;
+      } else {
+        q = m >> k;
+        const unsigned long long rem = m & ((1ull << k) - 1ull);
+        const unsigned long long half = 1ull << (k - 1);
+        if (rem > half || (rem == half && (q & 1ull))) ++q;
+      }
+    }
+  }
+  U = neg ? -static_cast<long long>(q) : static_cast<long long>(q);
+  return true;
+}
+
+// Support rule (Eq. 6): n_start = ceil(u - W/2) and S = (n_start - (u - W/2)) 2^32.
+__device__ __forceinline__ void support_start(long long U, int W, long long& n_start, unsigned& S) {
+  const long long Y = U - (W & 1) * (1ll << (kFracBits - 1));
+  const long long c = -((-Y) >> kFracBits);
+  n_start = c - (W >> 1);
+  S = static_cast<unsigned>((c << kFracBits) - Y);
+}
+
+// Lane t of the result holds bit l = bit t of lane l's input (32 x 32 bit transpose).
+__device__ __forceinline__ unsigned transpose32(unsigned x, int lane) {
+  const unsigned masks[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const int j = 16 >> k;
+    const unsigned m = masks[k];
+    const unsigned y = __shfl_xor_sync(0xffffffffu, x, j);
+    if (lane & j) x = (x & ~m) | ((y & ~m) >> j);
+    else          x = (x & m) | ((y & m) << j);
+  }
+  return x;
+}
+
+// Lanes [xrel, xrel + W) intersected with [0, 32).
+__device__ __forceinline__ unsigned cover_mask(int xrel, int W) {
+  const unsigned long long full = (1ull << W) - 1ull;
+  const unsigned long long m = xrel >= 0 ? (full << xrel) : (full >> (-xrel));
+  return static_cast<unsigned>(m);
+}
+
+// Table lookup (Section 5.1, Appendix F). Row k and fraction f come from the exact
+// integer product S * Ms (S in units of 2^-32): linear uses k = floor(t), f = t - k with
+// t = S Ms 2^-32; nearest uses row floor(t + 1/2). The table has Ms+1 rows of stride Wp.
+template <int W, typename R>
+__device__ __forceinline__ void table_weights(const R* __restrict__ tab, int Wp, int Ms, int interp,
+                                              unsigned S, R (&C)[W]) {
+  const unsigned long long P = static_cast<unsigned long long>(S) * static_cast<unsigned>(Ms);
+  if (interp) {
+    const int k = static_cast<int>(P >> 32);
+    const R f = static_cast<R>(static_cast<unsigned>(P & 0xffffffffull)) * static_cast<R>(2.3283064365386962890625e-10);
+    const R* r0 = tab + static_cast<size_t>(k) * Wp;
+    const R* r1 = r0 + Wp;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      const R a = r0[j];
+      C[j] = a + f * (r1[j] - a);
+    }
+  } else {
+    const int k = static_cast<int>((P + 0x80000000ull) >> 32);
+    const R* r0 = tab + static_cast<size_t>(k) * Wp;
+#pragma unroll
+    for (int j = 0; j < W; ++j) C[j] = r0[j];
+  }
+}
+
+__device__ __forceinline__ void red_add(float2* p, float2 v) {
+  asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ void red_add(double2* p, double2 v) {
+  atomicAdd(&p->x, v.x);
+  atomicAdd(&p->y, v.y);
+}
+
+}  // namespace lmg

@@ -1,0 +1,77 @@
+// Launch interfaces of the device kernels (host-callable, defined in the .cu files).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lmg {
+
+struct VisPos;
+struct Rec;
+struct Item;
+
+// counters[] slots (device ints, reset by bin_launch)
+enum { kCntBad = 0, kCntItems = 1, kCntSecondary = 2, kCntDupCursor = 3, kCntGridWork = 4, kCntDegridWork = 5 };
+
+struct BinArgs {
+  const double* uv;
+  long long nvis;
+  double scale2;  // N * pixel_scale * 2^32
+  int W, N, n_strips;
+  int rows_per_block, item_target, item_cap;
+  int max_blocks;
+  VisPos* pos;
+  int* hist;       // n_strips * N
+  int* offsets;    // n_strips * N + 1
+  int* cursor;     // n_strips * N
+  int* partial;    // scan chunk sums
+  Rec* recs;       // 2 * max_vis
+  int* dup_list;   // max_vis
+  int* bad_list;   // max_vis
+  Item* items;     // item_cap
+  int* counters;   // 8
+};
+
+int bin_launch(const BinArgs& a, cudaStream_t st);
+int bin_scan_chunks(long long L);
+
+struct SweepArgs {
+  const Rec* recs;
+  const int* offsets;
+  const Item* items;
+  int* counters;
+  const void* table;  // device, (Ms+1) x Wp of the plan's real type
+  int Wp, Ms, interp;
+  int N, n_strips;
+  int W;
+  int dtype;          // 0 float, 1 double
+  int accum;          // 0 plain, 1 compensated (float only)
+  int item_cap;
+  int grid_blocks;    // persistent CTAs
+  int table_in_smem;
+  // gridding
+  const void* vis;
+  const void* weights;
+  void* grid;
+  void* spill;        // item_cap * W * 32 complex
+  // degridding
+  const void* grid_in;
+  void* vis_out;
+  void* dpart;        // max_vis complex (secondary partial sums)
+  const int* dup_list;
+  const int* bad_list;
+  long long nvis;
+};
+
+int grid_launch(const SweepArgs& a, cudaStream_t st);
+int degrid_launch(const SweepArgs& a, cudaStream_t st);
+// Shared memory a sweep CTA needs (bytes) and CTAs per SM that fit; used to size launches.
+size_t sweep_smem_bytes(int W, int dtype, int Ms, bool table_in_smem, bool degrid);
+int sweep_set_smem_limits(int W, int dtype, int accum, size_t smem_bytes, bool degrid);
+int sweep_occupancy(int W, int dtype, int accum, size_t smem_bytes, bool degrid, int* blocks_per_sm);
+
+// Grid correction (Eqs. 4, 15) and its adjoint.
+int crop_correct_launch(const void* F, void* img, const void* h, int n_img, int N, int dtype, cudaStream_t st);
+int pad_correct_launch(const void* img, void* P, const void* h, int n_img, int N, int dtype, cudaStream_t st);
+
+}  // namespace lmg

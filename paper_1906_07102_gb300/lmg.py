@@ -1,0 +1,278 @@
+"""Thin ctypes binding of liblmg (include/lmg.h) for torch CUDA tensors.
+
+Argument marshalling only: every step of gridding, FFT, correction and degridding runs in
+the CUDA library. torch supplies device memory and the current stream. Loading fails
+loudly (RuntimeError) when the library has not been built; there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblmg.so")
+
+LMG_C64, LMG_C128 = 0, 1
+INTERP = {"nearest": 0, "linear": 1}
+CORRECTION = {"hopt": 0, "inv_c": 1}
+ACCUM = {"plain": 0, "compensated": 1}
+LMG_CROP, LMG_PAD = 0, 1
+FFT_IMAGE, FFT_MODEL = 1, -1
+
+_lib = None
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_SIGS = {
+    "lmg_kernel_table": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(_vp)]),
+    "lmg_table_from_values": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
+    "lmg_table_free": (ctypes.c_int, [_vp]),
+    "lmg_table_export": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, _vp, ctypes.c_size_t, _vp, _vp]),
+    "lmg_correction_export": (ctypes.c_int, [_vp, _i64, ctypes.c_int, _vp]),
+    "lmg_plan_create": (ctypes.c_int, [_vp, _i64, ctypes.c_double, _i64, ctypes.c_int, ctypes.POINTER(_vp)]),
+    "lmg_plan_free": (ctypes.c_int, [_vp]),
+    "lmg_plan_bin": (ctypes.c_int, [_vp, _vp, _i64, _vp]),
+    "lmg_plan_dropped": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), _vp]),
+    "lmg_plan_info": (ctypes.c_int, [_vp, _vp, _vp]),
+    "lmg_work_grid": (_vp, [_vp]),
+    "lmg_grid": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, _vp]),
+    "lmg_degrid": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "lmg_fft": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
+    "lmg_grid_correct": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
+    "lmg_dirty_image": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, _vp]),
+    "lmg_predict_vis": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "lmg_last_error": (ctypes.c_char_p, []),
+    "lmg_version": (ctypes.c_char_p, []),
+}
+EXPORTED = tuple(_SIGS)
+
+
+class LmgError(RuntimeError):
+    pass
+
+
+def lib():
+    """The loaded library (built in-tree by ``paper_1906_07102_gb300.build``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"liblmg.so not built ({LIB_PATH}); run python -m paper_1906_07102_gb300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise LmgError(f"lmg error {rc}: {lib().lmg_last_error().decode()}")
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _need(t, dtype, shape=None, name="tensor"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return t
+
+
+class Table:
+    """Least-misfit gridding function and look-up table (host float64)."""
+
+    def __init__(self, W, x0, oversample, interp="linear", correction="hopt", values=None):
+        h = ctypes.c_void_p()
+        if values is None:
+            _check(lib().lmg_kernel_table(W, x0, oversample, INTERP[interp], CORRECTION[correction], ctypes.byref(h)))
+        else:
+            v = np.ascontiguousarray(values, dtype=np.float64)
+            if v.shape != (oversample + 1, W):
+                raise ValueError("values must have shape (oversample + 1, W)")
+            _check(lib().lmg_table_from_values(W, x0, oversample, INTERP[interp], CORRECTION[correction],
+                                               v.ctypes.data_as(_vp), ctypes.byref(h)))
+        self._h = h
+        self.W, self.x0, self.oversample, self.interp = W, x0, oversample, interp
+
+    def export(self):
+        """(C [(Ms+1), W], h_nodes [33], E, info[4]) as numpy / floats."""
+        C = np.empty((self.oversample + 1, self.W))
+        h = np.empty(33)
+        E = ctypes.c_double()
+        info = (ctypes.c_int * 4)()
+        _check(lib().lmg_table_export(self._h, C.ctypes.data_as(_vp), C.size, h.ctypes.data_as(_vp), h.size,
+                                      ctypes.byref(E), info))
+        return C, h, E.value, list(info)
+
+    def correction(self, n_image, single_precision=False):
+        out = np.empty(n_image)
+        _check(lib().lmg_correction_export(self._h, n_image, int(bool(single_precision)), out.ctypes.data_as(_vp)))
+        return out
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.lmg_table_free(self._h)
+            self._h = None
+
+
+class Plan:
+    """Device state for one (table, image size, pixel scale); see lmg_plan_create."""
+
+    def __init__(self, table, n_image, pixel_scale, max_vis, dtype="c64"):
+        import torch
+        self.dtype_code = LMG_C64 if dtype == "c64" else LMG_C128
+        self.cdtype = torch.complex64 if self.dtype_code == LMG_C64 else torch.complex128
+        self.rdtype = torch.float32 if self.dtype_code == LMG_C64 else torch.float64
+        h = ctypes.c_void_p()
+        _check(lib().lmg_plan_create(table._h, n_image, pixel_scale, max_vis, self.dtype_code, ctypes.byref(h)))
+        self._h = h
+        self.table = table
+        self.n_image = n_image
+        self.N = int(round(n_image / table.x0))
+        self.W = table.W
+        self.nvis = None
+
+    def bin(self, uv):
+        import torch
+        uv = _need(uv, torch.float64, None, "uv")
+        if uv.dim() != 2 or uv.shape[1] != 2:
+            raise ValueError("uv must be [nvis, 2]")
+        _check(lib().lmg_plan_bin(self._h, _ptr(uv), uv.shape[0], _stream()))
+        self.nvis = uv.shape[0]
+        return self
+
+    def _vis_args(self, vis, weights):
+        vis = _need(vis, self.cdtype, (self.nvis,), "vis")
+        if weights is not None:
+            weights = _need(weights, self.rdtype, (self.nvis,), "weights")
+        return vis, weights
+
+    def grid(self, vis, weights=None, accum="plain", out=None):
+        import torch
+        vis, weights = self._vis_args(vis, weights)
+        if out is None:
+            out = torch.empty((self.N, self.N), dtype=self.cdtype, device=vis.device)
+        _need(out, self.cdtype, (self.N, self.N), "grid")
+        _check(lib().lmg_grid(self._h, _ptr(vis), _ptr(weights), ACCUM[accum], _ptr(out), _stream()))
+        return out
+
+    def degrid(self, grid, out=None):
+        import torch
+        _need(grid, self.cdtype, (self.N, self.N), "grid")
+        if out is None:
+            out = torch.empty(self.nvis, dtype=self.cdtype, device=grid.device)
+        _need(out, self.cdtype, (self.nvis,), "vis_out")
+        _check(lib().lmg_degrid(self._h, _ptr(grid), _ptr(out), _stream()))
+        return out
+
+    def fft(self, grid, direction):
+        _need(grid, self.cdtype, (self.N, self.N), "grid")
+        _check(lib().lmg_fft(self._h, FFT_IMAGE if direction == "image" else FFT_MODEL, _ptr(grid), _stream()))
+        return grid
+
+    def crop_correct(self, F, out=None):
+        import torch
+        _need(F, self.cdtype, (self.N, self.N), "F")
+        if out is None:
+            out = torch.empty((self.n_image, self.n_image), dtype=self.cdtype, device=F.device)
+        _need(out, self.cdtype, (self.n_image, self.n_image), "image")
+        _check(lib().lmg_grid_correct(self._h, LMG_CROP, _ptr(F), _ptr(out), _stream()))
+        return out
+
+    def pad_correct(self, image, out=None):
+        import torch
+        _need(image, self.cdtype, (self.n_image, self.n_image), "image")
+        if out is None:
+            out = torch.empty((self.N, self.N), dtype=self.cdtype, device=image.device)
+        _need(out, self.cdtype, (self.N, self.N), "grid")
+        _check(lib().lmg_grid_correct(self._h, LMG_PAD, _ptr(image), _ptr(out), _stream()))
+        return out
+
+    def dirty_image(self, vis, weights=None, accum="plain", out=None):
+        import torch
+        vis, weights = self._vis_args(vis, weights)
+        if out is None:
+            out = torch.empty((self.n_image, self.n_image), dtype=self.cdtype, device=vis.device)
+        _need(out, self.cdtype, (self.n_image, self.n_image), "image")
+        _check(lib().lmg_dirty_image(self._h, _ptr(vis), _ptr(weights), ACCUM[accum], _ptr(out), _stream()))
+        return out
+
+    def predict_vis(self, image, out=None):
+        import torch
+        _need(image, self.cdtype, (self.n_image, self.n_image), "image")
+        if out is None:
+            out = torch.empty(self.nvis, dtype=self.cdtype, device=image.device)
+        _need(out, self.cdtype, (self.nvis,), "vis_out")
+        _check(lib().lmg_predict_vis(self._h, _ptr(image), _ptr(out), _stream()))
+        return out
+
+    def dropped(self):
+        n = ctypes.c_int64()
+        _check(lib().lmg_plan_dropped(self._h, ctypes.byref(n), _stream()))
+        return n.value
+
+    def info(self):
+        out = (ctypes.c_int64 * 8)()
+        _check(lib().lmg_plan_info(self._h, out, _stream()))
+        keys = ["N", "n_image", "W", "nvis", "records", "items", "dtype"]
+        return dict(zip(keys, list(out)[:7]))
+
+    def work_grid(self):
+        return lib().lmg_work_grid(self._h)
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.lmg_plan_free(self._h)
+            self._h = None
+
+
+def _autograd():
+    import torch
+
+    class Predict(torch.autograd.Function):
+        """V = predict_vis(I) (pad, correct, FFT, degrid); its adjoint, the unweighted
+        dirty image, is the backward pass (the gridding sweep)."""
+
+        @staticmethod
+        def forward(ctx, image, plan):
+            ctx.plan = plan
+            ctx.real_input = not image.is_complex()
+            img = image.to(plan.cdtype).contiguous()
+            return plan.predict_vis(img)
+
+        @staticmethod
+        def backward(ctx, grad_vis):
+            plan = ctx.plan
+            g = plan.dirty_image(grad_vis.to(plan.cdtype).contiguous())
+            if ctx.real_input:
+                g = g.real.contiguous()
+            return g, None
+
+    return Predict
+
+
+_Predict = None
+
+
+def predict(image, plan):
+    """Differentiable prediction V = P I (torch.autograd); backward runs the gridding path."""
+    global _Predict
+    if _Predict is None:
+        _Predict = _autograd()
+    return _Predict.apply(image, plan)
