@@ -1,0 +1,410 @@
+"""Benchmark: least-misfit gridding + degridding throughput on one GB300 (or N replicas).
+
+One step = the whole hot path on one batch of visibilities: bin the positions, grid,
+FFT (+i), correct and crop to the dirty image; pad and correct a model image, FFT (-i),
+degrid to predicted visibilities. Workload: 64-antenna Earth-rotation tracks (6 h,
+2048 samples, 1.4 GHz; 4,128,768 visibilities), 4096^2 grid, 2048^2 image (x0 = 0.5),
+W = 7, linear table at M_s = 1000, complex64.
+
+Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle instead.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mvis/s grid+degrid at W=7, 4096² grid; fraction of roofline; RMS error vs FP64"
+WORKLOAD = dict(n_ant=64, hours=6.0, n_times=2048, freq_hz=1.4e9, n_src=200, noise_sigma=0.1,
+                N=4096, n_image=2048, x0=0.5, W=7, oversample=1000, interp="linear")
+WORKLOAD_NAME = ("64-antenna 6 h Earth-rotation tracks (2048 samples, 1.4 GHz, dec -30), 4,128,768 vis, "
+                 "200 point sources + noise, 4096^2 grid, 2048^2 image, W=7, linear table M_s=1000, complex64")
+L2_FLUSH_BYTES = 256 << 20
+KERNELS_PER_STEP = 12  # bin 6, grid sweep + spill 2, crop 1, pad 1, degrid sweep + fix-up 2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="run this many untimed steps only (for ncu launch lists) and exit")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_inputs():
+    from paper_1906_07102_gb300 import synthetic as S
+    w = WORKLOAD
+    uv = S.array_tracks(n_ant=w["n_ant"], hours=w["hours"], n_times=w["n_times"], freqs_hz=(w["freq_hz"],), seed=0)
+    dl = S.pixel_scale_for(uv)
+    l, m, f = S.point_source_sky(w["n_src"], 0.45 * w["n_image"] * dl, seed=0)
+    vis = S.visibilities(uv, l, m, f, noise_sigma=w["noise_sigma"], seed=0).astype(np.complex64)
+    model = S.gaussian_blob_image(w["n_image"], 64, seed=0).astype(np.complex64)
+    return uv, dl, vis, model
+
+
+# ---------------------------------------------------------------------------------------
+# oracle (CPU) timing: the reference arm and the cpu_baseline leg
+# ---------------------------------------------------------------------------------------
+_ORACLE_SETUP = {}
+
+
+def oracle_setup():
+    """The oracle's table and correction factors for the workload (built once, untimed)."""
+    if not _ORACLE_SETUP:
+        from oracle import design as D
+        from oracle import imaging as I
+        w = WORKLOAD
+        N, n_img, W, Ms = w["N"], w["n_image"], w["W"], w["oversample"]
+        h = D.least_misfit_h(W, w["x0"] / 2)
+        T = D.lm_table(h, W, w["x0"] / 2, Ms)
+        _ORACLE_SETUP["T"] = T
+        _ORACLE_SETUP["hv"] = D.correction_factors(T, Ms, D.INTERP_LINEAR, W, I.pixel_coords(n_img, N))
+    return _ORACLE_SETUP["T"], _ORACLE_SETUP["hv"]
+
+
+ORACLE_SAMPLE = 16  # the oracle processes every 16th visibility on the full 4096^2 grid
+
+
+def oracle_step_sample(uv, dl, vis, model):
+    """One oracle step (grid, FFT, crop, pad, FFT, degrid) on every ORACLE_SAMPLE-th
+    visibility, on the full grid; returns (visibilities processed, seconds)."""
+    from oracle import imaging as I
+    w = WORKLOAD
+    N, n_img, W, Ms = w["N"], w["n_image"], w["W"], w["oversample"]
+    T, hv = oracle_setup()
+    sel = np.arange(0, uv.shape[0], ORACLE_SAMPLE)
+    t0 = time.perf_counter()
+    uc = I.cells_from_wavelengths(uv[sel], N, dl)
+    plan = I.Plan(uc[:, 0], uc[:, 1], W, N)
+    img = I.dirty_image(plan, T, Ms, 1, hv, n_img, vis[sel].astype(np.complex128))
+    pv = I.predict_vis(plan, T, Ms, 1, hv, model.astype(np.complex128))
+    dt = time.perf_counter() - t0
+    assert np.isfinite(img).all() and np.isfinite(pv).all()
+    return sel.size, dt
+
+
+def oracle_sample_text(n, nv):
+    return (f"one oracle step on every {ORACLE_SAMPLE}th visibility ({n} of {nv}) with the full 4096^2 grid, "
+            f"FFTs and correction; value = visibilities of the sample per second; single-threaded numpy float64")
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    uv, dl, vis, model = make_inputs()
+    nv = uv.shape[0]
+    times = []
+    for _ in range(args.warmup):
+        oracle_step_sample(uv, dl, vis, model)
+    for _ in range(args.steps):
+        n, dt = oracle_step_sample(uv, dl, vis, model)
+        times.append(dt)
+    step_s = float(np.mean(times))
+    value = n / step_s / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mvis/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_s,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD_NAME, "parallelism": "none (host oracle)"},
+            "cpu_baseline": {"value": value, "unit": "Mvis/s", "cores": 1, "kind": "oracle",
+                             "sample": oracle_sample_text(n, nv)},
+            "e2e": {"value": value, "unit": "Mvis/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.proc = None
+        self.index = index
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(np.max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def traffic_record():
+    """DRAM traffic of the gridding pass from the committed ncu summary, if it was taken
+    on the current sweep source."""
+    p = os.path.join(ROOT, "profiles", "grid_sweep_config2_traffic.json")
+    try:
+        with open(p) as f:
+            rec = json.load(f)
+        src = open(os.path.join(ROOT, "paper_1906_07102_gb300", "csrc", "sweep.cu"), "rb").read()
+        if rec.get("sweep_cu_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        return float(rec["traffic_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def measured_peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def accuracy(uv, dl, vis, model, img, pv):
+    """Relative RMS error against the FP64 oracle on sampled outputs: 24 dirty-image pixels
+    (direct per-pixel evaluation) and 2000 predicted visibilities (full FP64 model grid)."""
+    from oracle import design as D
+    from oracle import imaging as I
+    w = WORKLOAD
+    N, n_img, W, Ms = w["N"], w["n_image"], w["W"], w["oversample"]
+    h = D.least_misfit_h(W, w["x0"] / 2)
+    T = D.lm_table(h, W, w["x0"] / 2, Ms)
+    x = I.pixel_coords(n_img, N)
+    g = np.random.default_rng(123)
+    py, px = g.integers(0, n_img, 24), g.integers(0, n_img, 24)
+    hx = D.correction_factors(T, Ms, 1, W, x[px])
+    hy = D.correction_factors(T, Ms, 1, W, x[py])
+    uc = I.cells_from_wavelengths(uv, N, dl)
+    plan = I.Plan(uc[:, 0], uc[:, 1], W, N)
+    ref_px = I.dirty_pixels_direct(plan, T, Ms, 1, hx, hy, vis.astype(np.complex128), None, x[px], x[py])
+    e_img = np.sqrt(np.mean(np.abs(img[py, px] - ref_px) ** 2) / np.mean(np.abs(ref_px) ** 2))
+    sel = g.integers(0, uv.shape[0], 2000)
+    hv = D.correction_factors(T, Ms, 1, W, x)
+    Gm = I.model_grid(I.pad_correct(model.astype(np.complex128), hv, N))
+    sub = I.Plan(uc[sel, 0], uc[sel, 1], W, N)
+    ref_pv = I.degrid(sub, T, Ms, 1, Gm)
+    e_pv = np.sqrt(np.mean(np.abs(pv[sel] - ref_pv) ** 2) / np.mean(np.abs(ref_pv) ** 2))
+    return {"dirty_image_rel_rms": float(e_img), "predicted_vis_rel_rms": float(e_pv),
+            "sample": "24 random pixels of the 2048^2 dirty image; 2000 random predicted visibilities"}
+
+
+def run_native(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_1906_07102_gb300 import lmg
+    w = WORKLOAD
+    uv, dl, vis, model = make_inputs()
+    nv = uv.shape[0]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    table = lmg.Table(w["W"], w["x0"], w["oversample"], w["interp"])
+    plan = lmg.Plan(table, w["n_image"], dl, nv, "c64")
+    uv_d = torch.from_numpy(uv).to(dev)
+    vis_d = torch.from_numpy(vis).to(dev)
+    model_d = torch.from_numpy(model).to(dev)
+    img_d = torch.empty((w["n_image"], w["n_image"]), dtype=torch.complex64, device=dev)
+    pv_d = torch.empty(nv, dtype=torch.complex64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.bin(uv_d)
+        plan.dirty_image(vis_d, out=img_d)
+        plan.predict_vis(model_d, out=pv_d)
+
+    if args.profile_steps:
+        for _ in range(args.profile_steps):
+            step()
+        torch.cuda.synchronize()
+        return
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    # timed region: K steps, L2 flushed before each (outside the step's events)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = Clocks(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        step()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    step_ms = float(np.mean([s.elapsed_time(e) for s, e in zip(starts, ends)]))
+    if world > 1:
+        t = torch.tensor([step_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        step_ms = float(t.item())
+    value = world * nv / (step_ms * 1e-3) / 1e6
+
+    # per-stage breakdown (untimed by the driver's clock; same stream, events per stage)
+    stages = {}
+
+    def timed(name, fn, reps=max(3, min(args.steps, 10))):
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        stages[name] = float(np.mean(ts))
+
+    work = torch.empty((w["N"], w["N"]), dtype=torch.complex64, device=dev)
+    timed("bin", lambda: plan.bin(uv_d))
+    timed("grid", lambda: plan.grid(vis_d, out=work))
+    timed("fft_image", lambda: plan.fft(work, "image"))
+    timed("crop_correct", lambda: plan.crop_correct(work, out=img_d))
+    timed("pad_correct", lambda: plan.pad_correct(model_d, out=work))
+    timed("fft_model", lambda: plan.fft(work, "model"))
+    timed("degrid", lambda: plan.degrid(work, out=pv_d))
+
+    # end to end through the public API with pinned host buffers
+    uv_h = torch.from_numpy(uv).pin_memory()
+    vis_h = torch.from_numpy(vis).pin_memory()
+    model_h = torch.from_numpy(model).pin_memory()
+    img_h = torch.empty(img_d.shape, dtype=img_d.dtype).pin_memory()
+    pv_h = torch.empty(pv_d.shape, dtype=pv_d.dtype).pin_memory()
+
+    def e2e_step():
+        uv_d.copy_(uv_h, non_blocking=True)
+        vis_d.copy_(vis_h, non_blocking=True)
+        model_d.copy_(model_h, non_blocking=True)
+        step()
+        img_h.copy_(img_d, non_blocking=True)
+        pv_h.copy_(pv_d, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    es, ee = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ek = max(3, min(args.steps, 10))
+    es.record(stream)
+    for _ in range(ek):
+        e2e_step()
+    ee.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = es.elapsed_time(ee) / ek
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    h2d = uv_h.numel() * 8 + vis_h.numel() * 8 + model_h.numel() * 8
+    d2h = img_h.numel() * 8 + pv_h.numel() * 8
+
+    # roofline of the gridding pass (sweep + spill): algorithmic bytes per launch
+    grid_bytes = nv * (16 + 8) + w["N"] * w["N"] * 8
+    peak, peak_src = measured_peak_hbm()
+    achieved = grid_bytes / (stages["grid"] * 1e-3) / 1e9
+    roof = {"kernel": "k_grid_sweep + k_grid_spill (gridding pass)", "bound": "hbm", "achieved": achieved,
+            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic_record(),
+            "algorithmic_bytes": grid_bytes, "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs, burst)"}
+    degrid_bytes = grid_bytes
+    extra = {"stages_ms": stages,
+             "grid_degrid_mvis_s": nv / ((stages["grid"] + stages["degrid"]) * 1e-3) / 1e6,
+             "degrid_roofline_frac": degrid_bytes / (stages["degrid"] * 1e-3) / 1e9 / peak,
+             "timed_wall_s": t_wall}
+
+    line = {"metric": METRIC, "value": value, "unit": "Mvis/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "nvis": nv, "grid": w["N"], "image": w["n_image"], "W": w["W"],
+                       "oversample": w["oversample"], "interp": w["interp"],
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "flushed before every timed step (256 MB write, outside the step's events)"},
+            "roofline": roof, "clocks": clk,
+            "e2e": {"value": world * nv / (e2e_ms * 1e-3) / 1e6, "unit": "Mvis/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": KERNELS_PER_STEP * args.steps}
+    line.update(extra)
+    if rank == 0 and not args.no_accuracy:
+        torch.cuda.synchronize()
+        step()
+        torch.cuda.synchronize()
+        line["accuracy_vs_fp64"] = accuracy(uv, dl, vis, model, img_d.cpu().numpy(), pv_d.cpu().numpy())
+    if rank == 0 and not args.no_cpu_baseline:
+        n, dt = oracle_step_sample(uv, dl, vis, model)
+        line["cpu_baseline"] = {"value": n / dt / 1e6, "unit": "Mvis/s", "cores": 1, "kind": "oracle",
+                                "sample": oracle_sample_text(n, nv) + f"; {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

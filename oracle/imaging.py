@@ -94,14 +94,20 @@ def grid(plan, T, Ms, interp, vis, weights=None):
     if weights is not None:
         wv = wv * np.asarray(weights, dtype=np.float64)
     G = np.zeros(N * N, dtype=np.complex128)
-    for j in range(W):
-        rows = (plan.m0 + j + N // 2) % N
-        for i in range(W):
-            cols = (plan.n0 + i + N // 2) % N
-            contrib = wv * Cv[:, j] * Cu[:, i]
-            flat = rows * N + cols
-            G += np.bincount(flat, weights=contrib.real, minlength=N * N)
-            G += 1j * np.bincount(flat, weights=contrib.imag, minlength=N * N)
+    chunk = max(1, (1 << 22) // (W * W))
+    for k0 in range(0, wv.size, chunk):
+        sl = slice(k0, k0 + chunk)
+        flat, contrib = [], []
+        for j in range(W):
+            rows = (plan.m0[sl] + j + N // 2) % N
+            for i in range(W):
+                cols = (plan.n0[sl] + i + N // 2) % N
+                flat.append(rows * N + cols)
+                contrib.append(wv[sl] * Cv[sl, j] * Cu[sl, i])
+        flat = np.concatenate(flat)
+        contrib = np.concatenate(contrib)
+        G += np.bincount(flat, weights=contrib.real, minlength=N * N)
+        G += 1j * np.bincount(flat, weights=contrib.imag, minlength=N * N)
     return G.reshape(N, N)
 
 

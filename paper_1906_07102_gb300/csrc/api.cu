@@ -34,15 +34,16 @@ struct lmg_plan {
   int64_t max_vis = 0, nvis = -1;
   int device = 0, sms = 0;
   int blocks_grid = 0, blocks_degrid = 0;
-  bool tab_smem = false;
-  size_t smem_grid = 0, smem_degrid = 0, smem_grid_comp = 0;
+  bool tab_smem_grid = false, tab_smem_degrid = false;
+  int warps_grid = 8, warps_degrid = 8;
+  size_t smem_grid = 0, smem_degrid = 0;
   int blocks_grid_comp = 0;
   void* d_table = nullptr;
   void* d_h = nullptr;
   VisPos* pos = nullptr;
   int* hist = nullptr;
   int* offsets = nullptr;
-  int* cursor = nullptr;
+  int2* rank = nullptr;
   int* partial = nullptr;
   Rec* recs = nullptr;
   int* dup_list = nullptr;
@@ -90,7 +91,7 @@ template <typename T> int dalloc(T** p, size_t count, const char* what) {
 
 void free_plan(lmg_plan* p) {
   if (!p) return;
-  void* ptrs[] = {p->d_table, p->d_h, p->pos, p->hist, p->offsets, p->cursor, p->partial, p->recs,
+  void* ptrs[] = {p->d_table, p->d_h, p->pos, p->hist, p->offsets, p->rank, p->partial, p->recs,
                   p->dup_list, p->bad_list, p->items, p->counters, p->spill, p->dpart, p->work};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -113,7 +114,6 @@ SweepArgs sweep_args(const lmg_plan* p) {
   a.W = p->W;
   a.dtype = p->dtype;
   a.item_cap = p->item_cap;
-  a.table_in_smem = p->tab_smem ? 1 : 0;
   a.dup_list = p->dup_list;
   a.bad_list = p->bad_list;
   a.nvis = p->nvis;
@@ -141,6 +141,8 @@ int do_grid(lmg_plan* p, const void* vis, const void* weights, int accum, void* 
   a.grid = grid;
   a.spill = p->spill;
   a.grid_blocks = accum ? p->blocks_grid_comp : p->blocks_grid;
+  a.warps = p->warps_grid;
+  a.table_in_smem = p->tab_smem_grid ? 1 : 0;
   return launch_status(grid_launch(a, st), "gridding");
 }
 
@@ -150,6 +152,8 @@ int do_degrid(lmg_plan* p, const void* grid, void* vis_out, cudaStream_t st) {
   a.vis_out = vis_out;
   a.dpart = p->dpart;
   a.grid_blocks = p->blocks_degrid;
+  a.warps = p->warps_degrid;
+  a.table_in_smem = p->tab_smem_degrid ? 1 : 0;
   return launch_status(degrid_launch(a, st), "degridding");
 }
 
@@ -337,12 +341,12 @@ int lmg_plan_create(const lmg_table* t, int64_t n_image, double pixel_scale, int
   if ((rc = dalloc(reinterpret_cast<unsigned char**>(&p->d_table), tab_bytes.size(), "table")) ||
       (rc = dalloc(reinterpret_cast<unsigned char**>(&p->d_h), h_bytes.size(), "correction")) ||
       (rc = dalloc(&p->pos, size_t(max_vis), "positions")) || (rc = dalloc(&p->hist, size_t(L), "histogram")) ||
-      (rc = dalloc(&p->offsets, size_t(L) + 1, "offsets")) || (rc = dalloc(&p->cursor, size_t(L), "cursor")) ||
+      (rc = dalloc(&p->offsets, size_t(L) + 1, "offsets")) || (rc = dalloc(&p->rank, size_t(max_vis), "ranks")) ||
       (rc = dalloc(&p->partial, size_t(p->nchunks), "scan")) || (rc = dalloc(&p->recs, size_t(2 * max_vis), "records")) ||
       (rc = dalloc(&p->dup_list, size_t(max_vis), "dup list")) ||
       (rc = dalloc(&p->bad_list, size_t(max_vis), "dropped list")) ||
-      (rc = dalloc(&p->items, size_t(p->item_cap), "items")) || (rc = dalloc(&p->counters, 8, "counters")) ||
-      (rc = dalloc(reinterpret_cast<unsigned char**>(&p->spill), size_t(p->item_cap) * p->W * kStrip * c2, "spill")) ||
+      (rc = dalloc(&p->items, size_t(p->item_cap), "items")) || (rc = dalloc(&p->counters, kNumCounters, "counters")) ||
+      (rc = dalloc(reinterpret_cast<unsigned char**>(&p->spill), size_t(p->item_cap) * ring_slots(p->W) * kStrip * c2, "spill")) ||
       (rc = dalloc(reinterpret_cast<unsigned char**>(&p->dpart), size_t(max_vis) * c2, "partials")) ||
       (rc = dalloc(reinterpret_cast<unsigned char**>(&p->work), size_t(N) * size_t(N) * c2, "work grid"))) {
     free_plan(p);
@@ -350,35 +354,35 @@ int lmg_plan_create(const lmg_table* t, int64_t n_image, double pixel_scale, int
   }
   if ((e = cudaMemcpy(p->d_table, tab_bytes.data(), tab_bytes.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(p->d_h, h_bytes.data(), h_bytes.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemset(p->counters, 0, 8 * sizeof(int))) != cudaSuccess) {
+      (e = cudaMemset(p->counters, 0, kNumCounters * sizeof(int))) != cudaSuccess) {
     free_plan(p);
     return cuda_fail(e, "plan upload");
   }
-  // Launch shapes: table in shared memory when it is small; persistent CTAs per SM.
-  p->tab_smem = tab_bytes.size() <= 64 * 1024;
-  p->smem_grid = sweep_smem_bytes(p->W, dtype, p->Ms, p->tab_smem, false);
-  p->smem_degrid = sweep_smem_bytes(p->W, dtype, p->Ms, p->tab_smem, true);
+  // Launch shapes: warps per CTA and table placement that fit shared memory; persistent
+  // CTAs per SM from the occupancy calculator.
+  const size_t kSmemLimit = 200 * 1024;
   int bps = 0;
-  if (sweep_set_smem_limits(p->W, dtype, 0, p->smem_grid, false) ||
-      sweep_set_smem_limits(p->W, dtype, 0, p->smem_degrid, true) ||
-      sweep_occupancy(p->W, dtype, 0, p->smem_grid, false, &bps)) {
+  if (sweep_config(p->W, dtype, p->Ms, false, kSmemLimit, &p->tab_smem_grid, &p->warps_grid) ||
+      sweep_config(p->W, dtype, p->Ms, true, kSmemLimit, &p->tab_smem_degrid, &p->warps_degrid)) {
     free_plan(p);
-    return cuda_fail(cudaGetLastError(), "sweep kernel attributes");
+    return set_error(LMG_EUNSUPPORTED, "sweep shared memory does not fit for this W and dtype");
   }
-  p->blocks_grid = p->sms * (bps > 0 ? bps : 1);
-  if (sweep_occupancy(p->W, dtype, 0, p->smem_degrid, true, &bps)) {
+  p->smem_grid = sweep_smem_bytes(p->W, dtype, p->Ms, p->tab_smem_grid, false, p->warps_grid);
+  p->smem_degrid = sweep_smem_bytes(p->W, dtype, p->Ms, p->tab_smem_degrid, true, p->warps_degrid);
+  for (int accum = 0; accum <= (dtype == LMG_C64 ? 1 : 0); ++accum) {
+    if (sweep_set_smem_limits(p->W, dtype, accum, p->smem_grid, false) ||
+        sweep_occupancy(p->W, dtype, accum, p->smem_grid, false, p->warps_grid, &bps)) {
+      free_plan(p);
+      return cuda_fail(cudaGetLastError(), "sweep kernel attributes");
+    }
+    (accum ? p->blocks_grid_comp : p->blocks_grid) = p->sms * (bps > 0 ? bps : 1);
+  }
+  if (sweep_set_smem_limits(p->W, dtype, 0, p->smem_degrid, true) ||
+      sweep_occupancy(p->W, dtype, 0, p->smem_degrid, true, p->warps_degrid, &bps)) {
     free_plan(p);
     return cuda_fail(cudaGetLastError(), "sweep kernel attributes");
   }
   p->blocks_degrid = p->sms * (bps > 0 ? bps : 1);
-  if (dtype == LMG_C64) {
-    if (sweep_set_smem_limits(p->W, dtype, 1, p->smem_grid, false) ||
-        sweep_occupancy(p->W, dtype, 1, p->smem_grid, false, &bps)) {
-      free_plan(p);
-      return cuda_fail(cudaGetLastError(), "sweep kernel attributes");
-    }
-    p->blocks_grid_comp = p->sms * (bps > 0 ? bps : 1);
-  }
   const cufftResult fr = cufftPlan2d(&p->fft, int(N), int(N), dtype == LMG_C128 ? CUFFT_Z2Z : CUFFT_C2C);
   if (fr != CUFFT_SUCCESS) {
     free_plan(p);
@@ -415,7 +419,7 @@ int lmg_plan_bin(lmg_plan* p, const double* uv, int64_t nvis, void* stream) {
   a.pos = p->pos;
   a.hist = p->hist;
   a.offsets = p->offsets;
-  a.cursor = p->cursor;
+  a.rank = p->rank;
   a.partial = p->partial;
   a.recs = p->recs;
   a.dup_list = p->dup_list;
@@ -455,7 +459,7 @@ int lmg_plan_info(lmg_plan* p, int64_t* out, void* stream) {
   out[2] = p->W;
   out[3] = p->nvis;
   out[4] = total;
-  out[5] = c[kCntItems];
+  out[5] = c[kCntItems] + c[kCntItemsBack];
   out[6] = p->dtype;
   return LMG_OK;
 }

@@ -4,10 +4,10 @@
 // Pipeline (all on one stream, no host synchronisation):
 //   1. k_bin_count   per visibility: float64 product to cells, exact fixed-point support
 //                    rule, strip keys (one, or two when the support crosses into the next
-//                    strip); bucket counts with warp-aggregated atomics.
+//                    strip); the bucket counter's returned value is the record's rank.
 //   2. scan          exclusive prefix sum of the bucket counts (strip-major, row-minor).
-//   3. k_bin_scatter records into their buckets (order inside a bucket is arbitrary).
-//   4. k_make_items  per strip and block of rows: items holding about kItemRecs records.
+//   3. k_bin_scatter records to offset + rank (order inside a bucket is arbitrary).
+//   4. k_make_items  per strip and block of rows: items holding about item_target records.
 #include <cuda_runtime.h>
 
 #include "device_common.cuh"
@@ -16,31 +16,33 @@
 namespace lmg {
 namespace {
 
-// Warp-aggregated atomicAdd of 1 to counter[key] for the lanes with key >= 0; returns
-// the old value plus the lane's rank among lanes with the same key. All 32 lanes call.
-__device__ __forceinline__ int agg_increment(int* counter, int key, int lane) {
-  const unsigned peers = __match_any_sync(0xffffffffu, key);
-  const int leader = __ffs(peers) - 1;
-  const int rank = __popc(peers & ((1u << lane) - 1u));
-  int old = 0;
-  if (lane == leader && key >= 0) old = atomicAdd(counter + key, __popc(peers));
-  old = __shfl_sync(0xffffffffu, old, leader);
-  return old + rank;
+// Appends the lanes with `take` to a list through one atomic per warp; returns the slot
+// of this lane (valid only when take). All 32 lanes call.
+__device__ __forceinline__ int warp_append(int* counter, bool take, int lane) {
+  const unsigned bal = __ballot_sync(0xffffffffu, take);
+  int base = 0;
+  if (lane == 0 && bal) base = atomicAdd(counter, __popc(bal));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  return base + __popc(bal & ((1u << lane) - 1u));
 }
 
+// Pass 1: positions to grid cells (support rule), bucket keys, and each record's rank in
+// its bucket (the value returned by the bucket counter), so that pass 2 needs no atomics.
 __global__ void k_bin_count(const double* __restrict__ uv, long long nvis, double scale2, int W,
-                            int N, int n_strips, VisPos* __restrict__ pos, int* __restrict__ hist,
-                            int* __restrict__ bad_list, int* __restrict__ counters) {
+                            int N, int n_strips, VisPos* __restrict__ pos, int2* __restrict__ rank,
+                            int* __restrict__ hist, int* __restrict__ bad_list, int* __restrict__ dup_list,
+                            int* __restrict__ counters) {
   const int lane = threadIdx.x & 31;
   const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
   for (long long base = static_cast<long long>(blockIdx.x) * blockDim.x; base < nvis; base += stride) {
     const long long k = base + threadIdx.x;
-    int key1 = -1, key2 = -1, bad = -1;
+    bool bad = false, dup = false;
     if (k < nvis) {
       long long U, V;
       const double2 p = reinterpret_cast<const double2*>(uv)[k];
       const bool ok = fixed_position(p.x, scale2, U) && fixed_position(p.y, scale2, V);
       VisPos vp;
+      int2 rk = make_int2(0, 0);
       if (ok) {
         long long n0, m0;
         support_start(U, W, n0, vp.su);
@@ -52,22 +54,24 @@ __global__ void k_bin_count(const double* __restrict__ uv, long long nvis, doubl
         vp.x0 = static_cast<int>(xi);
         vp.y0 = static_cast<int>(yi);
         const int strip = vp.x0 / kStrip;
-        key1 = strip * N + vp.y0;
-        if ((vp.x0 % kStrip) + W > kStrip) key2 = ((strip + 1) % n_strips) * N + vp.y0;
+        rk.x = atomicAdd(hist + strip * N + vp.y0, 1);
+        if ((vp.x0 % kStrip) + W > kStrip) {
+          dup = true;
+          rk.y = atomicAdd(hist + ((strip + 1) % n_strips) * N + vp.y0, 1);
+        }
       } else {
         vp.x0 = -1;
         vp.y0 = 0;
         vp.su = vp.sv = 0u;
-        bad = 0;
+        bad = true;
       }
       pos[k] = vp;
+      rank[k] = rk;
     }
-    agg_increment(hist, key1, lane);
-    agg_increment(hist, key2, lane);
-    const int bslot = agg_increment(counters, bad < 0 ? -1 : 0, lane);
-    if (bad >= 0) bad_list[bslot] = static_cast<int>(k);
-    // counters[2] counts secondary records (for the degrid fix-up list)
-    agg_increment(counters + 2, key2 >= 0 ? 0 : -1, lane);
+    const int bs = warp_append(counters + 0, bad, lane);
+    if (bad) bad_list[bs] = static_cast<int>(k);
+    const int ds = warp_append(counters + 2, dup, lane);
+    if (dup) dup_list[ds] = static_cast<int>(k);
   }
 }
 
@@ -127,10 +131,9 @@ __global__ void k_scan_top(int* __restrict__ partial, int nchunks) {
   }
 }
 
-// Stage 3: exclusive scan within each chunk plus the chunk offset; writes offsets[0..n]
-// and a copy into cursor[0..n).
+// Stage 3: exclusive scan within each chunk plus the chunk offset; writes offsets[0..n].
 __global__ void k_scan_final(const int* __restrict__ in, long long n, const int* __restrict__ partial,
-                             int* __restrict__ offsets, int* __restrict__ cursor) {
+                             int* __restrict__ offsets) {
   __shared__ int warp_sums[kScanThreads / 32];
   const long long base = static_cast<long long>(blockIdx.x) * kScanChunk + threadIdx.x * kScanPer;
   int v[kScanPer];
@@ -153,45 +156,35 @@ __global__ void k_scan_final(const int* __restrict__ in, long long n, const int*
   int run = partial[blockIdx.x] + woff + x - s;
 #pragma unroll
   for (int i = 0; i < kScanPer; ++i) {
-    if (base + i < n) {
-      offsets[base + i] = run;
-      cursor[base + i] = run;
-    }
+    if (base + i < n) offsets[base + i] = run;
     run += v[i];
   }
   if (base + kScanPer >= n && base < n) offsets[n] = run;  // thread holding the last element
 }
 
-__global__ void k_bin_scatter(const VisPos* __restrict__ pos, long long nvis, int W, int N, int n_strips,
-                              int* __restrict__ cursor, Rec* __restrict__ recs, int* __restrict__ dup_list,
-                              int* __restrict__ counters) {
-  const int lane = threadIdx.x & 31;
+// Pass 2: every record to offsets[bucket] + rank (no atomics).
+__global__ void k_bin_scatter(const VisPos* __restrict__ pos, const int2* __restrict__ rank, long long nvis,
+                              int W, int N, int n_strips, const int* __restrict__ offsets,
+                              Rec* __restrict__ recs) {
   const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
-  for (long long base = static_cast<long long>(blockIdx.x) * blockDim.x; base < nvis; base += stride) {
-    const long long k = base + threadIdx.x;
-    int key1 = -1, key2 = -1;
-    VisPos vp{-1, 0, 0u, 0u};
-    if (k < nvis) {
-      vp = pos[k];
-      if (vp.x0 >= 0) {
-        const int strip = vp.x0 / kStrip;
-        key1 = strip * N + vp.y0;
-        if ((vp.x0 % kStrip) + W > kStrip) key2 = ((strip + 1) % n_strips) * N + vp.y0;
-      }
-    }
-    const int s1 = agg_increment(cursor, key1, lane);
-    const int s2 = agg_increment(cursor, key2, lane);
-    const int sd = agg_increment(counters + 3, key2 >= 0 ? 0 : -1, lane);
-    if (key1 >= 0) recs[s1] = Rec{static_cast<unsigned>(k), vp.x0 % kStrip, vp.su, vp.sv};
-    if (key2 >= 0) {
-      recs[s2] = Rec{static_cast<unsigned>(k), (vp.x0 % kStrip) - kStrip, vp.su, vp.sv};
-      dup_list[sd] = static_cast<int>(k);
+  for (long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; k < nvis; k += stride) {
+    const VisPos vp = pos[k];
+    if (vp.x0 < 0) continue;
+    const int2 rk = rank[k];
+    const int strip = vp.x0 / kStrip, xr = vp.x0 % kStrip;
+    recs[offsets[strip * N + vp.y0] + rk.x] = Rec{static_cast<unsigned>(k), rec_pack(vp.y0, xr), vp.su, vp.sv};
+    if (xr + W > kStrip) {
+      const int s2 = (strip + 1) % n_strips;
+      recs[offsets[s2 * N + vp.y0] + rk.y] = Rec{static_cast<unsigned>(k), rec_pack(vp.y0, xr - kStrip), vp.su, vp.sv};
     }
   }
 }
 
 // One thread per (strip, block of rows): cut the block into items of about `target`
 // records each (at least one item per block), by binary search on the row offsets.
+// Items with more than target/2 records are placed from the front of the array and the
+// others from the back, so that the sweeps (which take items front to back, then back to
+// front) start the heavy ones first.
 __global__ void k_make_items(const int* __restrict__ offsets, int N, int n_strips, int rows_per_block,
                              int target, Item* __restrict__ items, int* __restrict__ counters, int cap) {
   const int nblk = (N + rows_per_block - 1) / rows_per_block;
@@ -203,8 +196,7 @@ __global__ void k_make_items(const int* __restrict__ offsets, int N, int n_strip
   const int o0 = off[rb], o1 = off[re];
   const int count = o1 - o0;
   const int m = max(1, (count + target - 1) / target);
-  const int slot = atomicAdd(counters + 1, m);
-  int prev = rb;
+  int prev = rb, prev_off = o0;
   for (int k = 0; k < m; ++k) {
     int next = re;
     if (k + 1 < m) {
@@ -217,8 +209,14 @@ __global__ void k_make_items(const int* __restrict__ offsets, int N, int n_strip
       }
       next = lo;
     }
-    if (slot + k < cap) items[slot + k] = Item{s, prev, next, 0};
+    const int next_off = off[next];
+    const int n = next_off - prev_off;
+    int slot;
+    if (2 * n > target) slot = atomicAdd(counters + kCntItems, 1);
+    else slot = cap - 1 - atomicAdd(counters + kCntItemsBack, 1);
+    if (slot >= 0 && slot < cap) items[slot] = Item{s, prev, next, n};
     prev = next;
+    prev_off = next_off;
   }
 }
 
@@ -227,18 +225,17 @@ __global__ void k_make_items(const int* __restrict__ offsets, int N, int n_strip
 int bin_launch(const BinArgs& a, cudaStream_t st) {
   const long long L = static_cast<long long>(a.n_strips) * a.N;
   cudaMemsetAsync(a.hist, 0, sizeof(int) * L, st);
-  cudaMemsetAsync(a.counters, 0, sizeof(int) * 8, st);
+  cudaMemsetAsync(a.counters, 0, sizeof(int) * kNumCounters, st);
   const int threads = 256;
   const long long want = (a.nvis + threads - 1) / threads;
   const int blocks = static_cast<int>(want < a.max_blocks ? (want > 0 ? want : 1) : a.max_blocks);
-  k_bin_count<<<blocks, threads, 0, st>>>(a.uv, a.nvis, a.scale2, a.W, a.N, a.n_strips, a.pos, a.hist,
-                                          a.bad_list, a.counters);
+  k_bin_count<<<blocks, threads, 0, st>>>(a.uv, a.nvis, a.scale2, a.W, a.N, a.n_strips, a.pos, a.rank, a.hist,
+                                          a.bad_list, a.dup_list, a.counters);
   const int nchunks = static_cast<int>((L + kScanChunk - 1) / kScanChunk);
   k_scan_partials<<<nchunks, kScanThreads, 0, st>>>(a.hist, L, a.partial);
   k_scan_top<<<1, 1024, 0, st>>>(a.partial, nchunks);
-  k_scan_final<<<nchunks, kScanThreads, 0, st>>>(a.hist, L, a.partial, a.offsets, a.cursor);
-  k_bin_scatter<<<blocks, threads, 0, st>>>(a.pos, a.nvis, a.W, a.N, a.n_strips, a.cursor, a.recs, a.dup_list,
-                                            a.counters);
+  k_scan_final<<<nchunks, kScanThreads, 0, st>>>(a.hist, L, a.partial, a.offsets);
+  k_bin_scatter<<<blocks, threads, 0, st>>>(a.pos, a.rank, a.nvis, a.W, a.N, a.n_strips, a.offsets, a.recs);
   const int nblk = (a.N + a.rows_per_block - 1) / a.rows_per_block;
   const int ntask = a.n_strips * nblk;
   k_make_items<<<(ntask + 127) / 128, 128, 0, st>>>(a.offsets, a.N, a.n_strips, a.rows_per_block, a.item_target,

@@ -17,18 +17,22 @@ struct VisPos {
   unsigned su, sv;
 };
 
-// One binned record: a visibility as seen from one 32-column strip. xrel is the support
-// start column relative to the strip's first column (negative when the support started
-// in the previous strip, i.e. for the strip's secondary copy).
+// One binned record: a visibility as seen from one 32-column strip. rx packs the
+// support-start row (bits 8..31) and xrel (bits 0..7, signed), the support start column
+// relative to the strip's first column (negative when the support started in the
+// previous strip, i.e. for the strip's secondary copy).
 struct Rec {
   unsigned idx;
-  int xrel;
+  int rx;
   unsigned su, sv;
 };
+__host__ __device__ __forceinline__ int rec_pack(int row, int xrel) { return (row << 8) | (xrel & 0xff); }
+__host__ __device__ __forceinline__ int rec_xrel(int rx) { return static_cast<int>(static_cast<signed char>(rx & 0xff)); }
+__host__ __device__ __forceinline__ int rec_row(int rx) { return static_cast<int>(static_cast<unsigned>(rx) >> 8); }
 
-// Work item: rows [r0, r1) of one strip.
+// Work item: rows [r0, r1) of one strip holding nrec records.
 struct Item {
-  int strip, r0, r1, pad;
+  int strip, r0, r1, nrec;
 };
 
 template <typename R> struct Cplx;
@@ -120,6 +124,30 @@ __device__ __forceinline__ void table_weights(const R* __restrict__ tab, int Wp,
 #pragma unroll
     for (int j = 0; j < W; ++j) C[j] = r0[j];
   }
+}
+
+// Packed single-precision pairs (re, im) in one 64-bit register: Blackwell's f32x2 FMA
+// does a complex-by-real multiply-add in one instruction.
+__device__ __forceinline__ unsigned long long f2pack(float x, float y) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+  return r;
+}
+__device__ __forceinline__ float2 f2unpack(unsigned long long r) {
+  float2 v;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+  return v;
+}
+// a * b + c, elementwise on the two halves
+__device__ __forceinline__ unsigned long long f2fma(unsigned long long a, unsigned long long b, unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2mul(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
 }
 
 __device__ __forceinline__ void red_add(float2* p, float2 v) {

@@ -11,7 +11,15 @@ struct Rec;
 struct Item;
 
 // counters[] slots (device ints, reset by bin_launch)
-enum { kCntBad = 0, kCntItems = 1, kCntSecondary = 2, kCntDupCursor = 3, kCntGridWork = 4, kCntDegridWork = 5 };
+enum {
+  kCntBad = 0,         // dropped positions (bad_list length)
+  kCntItems = 1,       // items placed from the front (heavy)
+  kCntSecondary = 2,   // visibilities with a second-strip record (dup_list length)
+  kCntItemsBack = 3,   // items placed from the back (light)
+  kCntGridWork = 4,    // work counter of the gridding sweep
+  kCntDegridWork = 5,  // work counter of the degridding sweep
+  kNumCounters = 8
+};
 
 struct BinArgs {
   const double* uv;
@@ -23,7 +31,7 @@ struct BinArgs {
   VisPos* pos;
   int* hist;       // n_strips * N
   int* offsets;    // n_strips * N + 1
-  int* cursor;     // n_strips * N
+  int2* rank;      // max_vis: rank of the record(s) in their buckets
   int* partial;    // scan chunk sums
   Rec* recs;       // 2 * max_vis
   int* dup_list;   // max_vis
@@ -48,6 +56,7 @@ struct SweepArgs {
   int accum;          // 0 plain, 1 compensated (float only)
   int item_cap;
   int grid_blocks;    // persistent CTAs
+  int warps;          // warps per CTA (1..8)
   int table_in_smem;
   // gridding
   const void* vis;
@@ -64,11 +73,15 @@ struct SweepArgs {
 };
 
 int grid_launch(const SweepArgs& a, cudaStream_t st);
+// Rows held in the sweep's rolling ring for support W (spill buffer rows per item).
+int ring_slots(int W);
 int degrid_launch(const SweepArgs& a, cudaStream_t st);
 // Shared memory a sweep CTA needs (bytes) and CTAs per SM that fit; used to size launches.
-size_t sweep_smem_bytes(int W, int dtype, int Ms, bool table_in_smem, bool degrid);
+size_t sweep_smem_bytes(int W, int dtype, int Ms, bool table_in_smem, bool degrid, int warps);
 int sweep_set_smem_limits(int W, int dtype, int accum, size_t smem_bytes, bool degrid);
-int sweep_occupancy(int W, int dtype, int accum, size_t smem_bytes, bool degrid, int* blocks_per_sm);
+int sweep_occupancy(int W, int dtype, int accum, size_t smem_bytes, bool degrid, int warps, int* blocks_per_sm);
+// Warps per CTA and table placement so that a CTA's shared memory stays within `limit`.
+int sweep_config(int W, int dtype, int Ms, bool degrid, size_t limit, bool* table_in_smem, int* warps);
 
 // Grid correction (Eqs. 4, 15) and its adjoint.
 int crop_correct_launch(const void* F, void* img, const void* h, int n_img, int N, int dtype, cudaStream_t st);
