@@ -188,6 +188,33 @@ int lmg_plan_info(lmg_plan* p, int64_t* out, void* stream);
  * lmg_plan_free); holds the FFT-domain grid after lmg_dirty_image / lmg_predict_vis. */
 void* lmg_work_grid(lmg_plan* p);
 
+/* lmg_grid_static -- binning plus gridding (the work of lmg_plan_bin + lmg_grid, complex64)
+ * without allocating any memory, for callers that cannot call cudaMalloc: for example a
+ * process whose device memory is owned by another allocator or reserved at start-up, or
+ * a real-time pipeline that must not allocate while it runs. The paper has no
+ * counterpart; this is a deployment variant of the existing path.
+ *
+ * All working memory (positions, records, bucket counts, work items, spill rows and the
+ * float32 copy of the table) lives in one fixed-size __device__ array of this library,
+ * about 22 MB, which every GPU that loads the library holds until the process exits.
+ * Limits: nvis <= LMG_STATIC_MAX_VIS, grid N = n_image / x0 a multiple of 32 in
+ * [64, LMG_STATIC_MAX_N], table oversample <= LMG_STATIC_MAX_OVERSAMPLE; larger sizes
+ * return LMG_EINVAL with a message and do nothing.
+ *   t            table (host object from lmg_kernel_table or lmg_table_from_values)
+ *   n_image, pixel_scale, uv, nvis   as for lmg_plan_create / lmg_plan_bin
+ *   vis          device complex64 [nvis]; weights device float32 [nvis] or NULL
+ *   grid         device complex64 [N][N]; every cell is overwritten
+ * The first call on a device (with that device current) looks up the array's device
+ * address and records it; make that first call before any stream capture. All calls
+ * share the one array: calls whose GPU work overlaps (other streams, other host threads)
+ * race on it and must be serialised by the caller. Nothing is carried between calls
+ * (bucket counts and counters are cleared on the stream by each call). */
+#define LMG_STATIC_MAX_VIS 262144
+#define LMG_STATIC_MAX_N 2048
+#define LMG_STATIC_MAX_OVERSAMPLE 4096
+int lmg_grid_static(const lmg_table* t, int64_t n_image, double pixel_scale, const double* uv,
+                    int64_t nvis, const void* vis, const void* weights, void* grid, void* stream);
+
 /* lmg_last_error -- message for the calling thread's most recent failure ("" if none). */
 const char* lmg_last_error(void);
 

@@ -42,6 +42,7 @@ _SIGS = {
     "lmg_grid_correct": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
     "lmg_dirty_image": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, _vp]),
     "lmg_predict_vis": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "lmg_grid_static": (ctypes.c_int, [_vp, _i64, ctypes.c_double, _vp, _i64, _vp, _vp, _vp, _vp]),
     "lmg_last_error": (ctypes.c_char_p, []),
     "lmg_version": (ctypes.c_char_p, []),
 }
@@ -240,6 +241,29 @@ class Plan:
         if getattr(self, "_h", None) and _lib is not None:
             _lib.lmg_plan_free(self._h)
             self._h = None
+
+
+STATIC_MAX_VIS = 262144
+STATIC_MAX_N = 2048
+
+
+def grid_static(table, n_image, pixel_scale, uv, vis, weights=None, out=None):
+    """Binning plus gridding through lmg_grid_static (complex64): the same result as
+    Plan.bin + Plan.grid, with no device allocation inside the library (all working memory
+    is a fixed array of the library; see include/lmg.h for the limits)."""
+    import torch
+    uv = _need(uv, torch.float64, None, "uv")
+    nvis = uv.shape[0]
+    vis = _need(vis, torch.complex64, (nvis,), "vis")
+    if weights is not None:
+        weights = _need(weights, torch.float32, (nvis,), "weights")
+    N = int(round(n_image / table.x0))
+    if out is None:
+        out = torch.empty((N, N), dtype=torch.complex64, device=vis.device)
+    _need(out, torch.complex64, (N, N), "grid")
+    _check(lib().lmg_grid_static(table._h, n_image, pixel_scale, _ptr(uv), nvis, _ptr(vis), _ptr(weights),
+                                 _ptr(out), _stream()))
+    return out
 
 
 def _autograd():
