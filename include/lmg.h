@@ -196,7 +196,7 @@ void* lmg_work_grid(lmg_plan* p);
  *
  * All working memory (positions, records, bucket counts, work items, spill rows and the
  * float32 copy of the table) lives in one fixed-size __device__ array of this library,
- * about 22 MB, which every GPU that loads the library holds until the process exits.
+ * about 20 MB, which every GPU that loads the library holds until the process exits.
  * Limits: nvis <= LMG_STATIC_MAX_VIS, grid N = n_image / x0 a multiple of 32 in
  * [64, LMG_STATIC_MAX_N], table oversample <= LMG_STATIC_MAX_OVERSAMPLE; larger sizes
  * return LMG_EINVAL with a message and do nothing.

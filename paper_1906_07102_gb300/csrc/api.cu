@@ -46,8 +46,6 @@ struct lmg_plan {
   int2* rank = nullptr;
   int* partial = nullptr;
   Rec* recs = nullptr;
-  int* dup_list = nullptr;
-  int* bad_list = nullptr;
   Item* items = nullptr;
   int* counters = nullptr;
   void* spill = nullptr;
@@ -92,7 +90,7 @@ template <typename T> int dalloc(T** p, size_t count, const char* what) {
 void free_plan(lmg_plan* p) {
   if (!p) return;
   void* ptrs[] = {p->d_table, p->d_h, p->pos, p->hist, p->offsets, p->rank, p->partial, p->recs,
-                  p->dup_list, p->bad_list, p->items, p->counters, p->spill, p->dpart, p->work};
+                  p->items, p->counters, p->spill, p->dpart, p->work};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->fft_ok) cufftDestroy(p->fft);
@@ -114,8 +112,7 @@ SweepArgs sweep_args(const lmg_plan* p) {
   a.W = p->W;
   a.dtype = p->dtype;
   a.item_cap = p->item_cap;
-  a.dup_list = p->dup_list;
-  a.bad_list = p->bad_list;
+  a.pos = p->pos;
   a.nvis = p->nvis;
   return a;
 }
@@ -343,8 +340,6 @@ int lmg_plan_create(const lmg_table* t, int64_t n_image, double pixel_scale, int
       (rc = dalloc(&p->pos, size_t(max_vis), "positions")) || (rc = dalloc(&p->hist, size_t(L), "histogram")) ||
       (rc = dalloc(&p->offsets, size_t(L) + 1, "offsets")) || (rc = dalloc(&p->rank, size_t(max_vis), "ranks")) ||
       (rc = dalloc(&p->partial, size_t(p->nchunks), "scan")) || (rc = dalloc(&p->recs, size_t(2 * max_vis), "records")) ||
-      (rc = dalloc(&p->dup_list, size_t(max_vis), "dup list")) ||
-      (rc = dalloc(&p->bad_list, size_t(max_vis), "dropped list")) ||
       (rc = dalloc(&p->items, size_t(p->item_cap), "items")) || (rc = dalloc(&p->counters, kNumCounters, "counters")) ||
       (rc = dalloc(reinterpret_cast<unsigned char**>(&p->spill), size_t(p->item_cap) * ring_slots(p->W) * kStrip * c2, "spill")) ||
       (rc = dalloc(reinterpret_cast<unsigned char**>(&p->dpart), size_t(max_vis) * c2, "partials")) ||
@@ -422,8 +417,6 @@ int lmg_plan_bin(lmg_plan* p, const double* uv, int64_t nvis, void* stream) {
   a.rank = p->rank;
   a.partial = p->partial;
   a.recs = p->recs;
-  a.dup_list = p->dup_list;
-  a.bad_list = p->bad_list;
   a.items = p->items;
   a.counters = p->counters;
   const int rc = launch_status(bin_launch(a, static_cast<cudaStream_t>(stream)), "binning");

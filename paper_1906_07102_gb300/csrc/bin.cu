@@ -16,62 +16,65 @@
 namespace lmg {
 namespace {
 
-// Appends the lanes with `take` to a list through one atomic per warp; returns the slot
-// of this lane (valid only when take). All 32 lanes call.
-__device__ __forceinline__ int warp_append(int* counter, bool take, int lane) {
-  const unsigned bal = __ballot_sync(0xffffffffu, take);
-  int base = 0;
-  if (lane == 0 && bal) base = atomicAdd(counter, __popc(bal));
-  base = __shfl_sync(0xffffffffu, base, 0);
-  return base + __popc(bal & ((1u << lane) - 1u));
-}
-
 // Pass 1: positions to grid cells (support rule), bucket keys, and each record's rank in
 // its bucket (the value returned by the bucket counter), so that pass 2 needs no atomics.
+// Each thread takes kCountIlp positions per iteration so that their bucket atomics are in
+// flight together.
+constexpr int kCountIlp = 4;
+
 __global__ void k_bin_count(const double* __restrict__ uv, long long nvis, double scale2, int W,
                             int N, int n_strips, VisPos* __restrict__ pos, int2* __restrict__ rank,
-                            int* __restrict__ hist, int* __restrict__ bad_list, int* __restrict__ dup_list,
-                            int* __restrict__ counters) {
-  const int lane = threadIdx.x & 31;
-  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
-  for (long long base = static_cast<long long>(blockIdx.x) * blockDim.x; base < nvis; base += stride) {
-    const long long k = base + threadIdx.x;
-    bool bad = false, dup = false;
-    if (k < nvis) {
-      long long U, V;
-      const double2 p = reinterpret_cast<const double2*>(uv)[k];
-      const bool ok = fixed_position(p.x, scale2, U) && fixed_position(p.y, scale2, V);
-      VisPos vp;
-      int2 rk = make_int2(0, 0);
-      if (ok) {
-        long long n0, m0;
-        support_start(U, W, n0, vp.su);
-        support_start(V, W, m0, vp.sv);
-        long long xi = (n0 + N / 2) % N;
-        long long yi = (m0 + N / 2) % N;
-        if (xi < 0) xi += N;
-        if (yi < 0) yi += N;
-        vp.x0 = static_cast<int>(xi);
-        vp.y0 = static_cast<int>(yi);
-        const int strip = vp.x0 / kStrip;
-        rk.x = atomicAdd(hist + strip * N + vp.y0, 1);
-        if ((vp.x0 % kStrip) + W > kStrip) {
-          dup = true;
-          rk.y = atomicAdd(hist + ((strip + 1) % n_strips) * N + vp.y0, 1);
+                            int* __restrict__ hist, int* __restrict__ counters) {
+  const int lane = threadIdx.x & 31;  // for the dropped-position count
+  const long long span = static_cast<long long>(blockDim.x) * kCountIlp;
+  const long long stride = static_cast<long long>(gridDim.x) * span;
+  for (long long base = static_cast<long long>(blockIdx.x) * span; base < nvis; base += stride) {
+    VisPos vp[kCountIlp];
+    int key1[kCountIlp], key2[kCountIlp];
+    bool bad[kCountIlp];
+#pragma unroll
+    for (int u = 0; u < kCountIlp; ++u) {
+      const long long k = base + u * blockDim.x + threadIdx.x;
+      key1[u] = key2[u] = -1;
+      bad[u] = false;
+      vp[u] = VisPos{-1, 0, 0u, 0u};
+      if (k < nvis) {
+        long long U, V;
+        const double2 p = reinterpret_cast<const double2*>(uv)[k];
+        if (fixed_position(p.x, scale2, U) && fixed_position(p.y, scale2, V)) {
+          long long n0, m0;
+          support_start(U, W, n0, vp[u].su);
+          support_start(V, W, m0, vp[u].sv);
+          long long xi = (n0 + N / 2) % N;
+          long long yi = (m0 + N / 2) % N;
+          if (xi < 0) xi += N;
+          if (yi < 0) yi += N;
+          vp[u].x0 = static_cast<int>(xi);
+          vp[u].y0 = static_cast<int>(yi);
+          const int strip = vp[u].x0 / kStrip;
+          key1[u] = strip * N + vp[u].y0;
+          if ((vp[u].x0 % kStrip) + W > kStrip) key2[u] = ((strip + 1) % n_strips) * N + vp[u].y0;
+        } else {
+          bad[u] = true;
         }
-      } else {
-        vp.x0 = -1;
-        vp.y0 = 0;
-        vp.su = vp.sv = 0u;
-        bad = true;
       }
-      pos[k] = vp;
-      rank[k] = rk;
     }
-    const int bs = warp_append(counters + 0, bad, lane);
-    if (bad) bad_list[bs] = static_cast<int>(k);
-    const int ds = warp_append(counters + 2, dup, lane);
-    if (dup) dup_list[ds] = static_cast<int>(k);
+    int2 rk[kCountIlp];
+#pragma unroll
+    for (int u = 0; u < kCountIlp; ++u) {
+      rk[u].x = key1[u] >= 0 ? atomicAdd(hist + key1[u], 1) : 0;
+      rk[u].y = key2[u] >= 0 ? atomicAdd(hist + key2[u], 1) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < kCountIlp; ++u) {
+      const long long k = base + u * blockDim.x + threadIdx.x;
+      if (k < nvis) {
+        pos[k] = vp[u];
+        rank[k] = rk[u];
+      }
+      const unsigned nb = __popc(__ballot_sync(0xffffffffu, bad[u]));
+      if (lane == 0 && nb) atomicAdd(counters + kCntBad, static_cast<int>(nb));
+    }
   }
 }
 
@@ -180,43 +183,45 @@ __global__ void k_bin_scatter(const VisPos* __restrict__ pos, const int2* __rest
   }
 }
 
-// One thread per (strip, block of rows): cut the block into items of about `target`
-// records each (at least one item per block), by binary search on the row offsets.
-// Items with more than target/2 records are placed from the front of the array and the
-// others from the back, so that the sweeps (which take items front to back, then back to
-// front) start the heavy ones first.
+// One CTA per (strip, block of rows): the block's row offsets are staged in shared memory
+// and the block is cut into items of about `target` records each (at least one item per
+// block) by binary searches there, one item per thread. Items with more than target/2
+// records are placed from the front of the array and the others from the back, so that
+// the sweeps (which take items front to back, then back to front) start the heavy ones
+// first.
+constexpr int kMaxRowsPerBlock = 256;
+
 __global__ void k_make_items(const int* __restrict__ offsets, int N, int n_strips, int rows_per_block,
                              int target, Item* __restrict__ items, int* __restrict__ counters, int cap) {
+  __shared__ int s_off[kMaxRowsPerBlock + 1];
   const int nblk = (N + rows_per_block - 1) / rows_per_block;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n_strips * nblk) return;
-  const int s = t / nblk, b = t % nblk;
+  const int s = blockIdx.x / nblk, b = blockIdx.x % nblk;
   const int rb = b * rows_per_block, re = min(N, rb + rows_per_block);
   const int* off = offsets + static_cast<long long>(s) * N;
-  const int o0 = off[rb], o1 = off[re];
-  const int count = o1 - o0;
+  for (int r = threadIdx.x; r <= re - rb; r += blockDim.x) s_off[r] = off[rb + r];
+  __syncthreads();
+  const int o0 = s_off[0], count = s_off[re - rb] - o0;
   const int m = max(1, (count + target - 1) / target);
-  int prev = rb, prev_off = o0;
-  for (int k = 0; k < m; ++k) {
-    int next = re;
-    if (k + 1 < m) {
-      const long long goal = o0 + (static_cast<long long>(count) * (k + 1)) / m;
-      int lo = prev, hi = re;  // first row r in [prev, re] with off[r] >= goal
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (off[mid] >= goal) hi = mid;
-        else lo = mid + 1;
-      }
-      next = lo;
+  // first row (relative) whose offset reaches the k-th cut
+  auto cut = [&](int k) {
+    if (k <= 0) return 0;
+    if (k >= m) return re - rb;
+    const long long goal = o0 + (static_cast<long long>(count) * k) / m;
+    int lo = 0, hi = re - rb;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (s_off[mid] >= goal) hi = mid;
+      else lo = mid + 1;
     }
-    const int next_off = off[next];
-    const int n = next_off - prev_off;
+    return lo;
+  };
+  for (int k = threadIdx.x; k < m; k += blockDim.x) {
+    const int r0 = cut(k), r1 = cut(k + 1);
+    const int n = s_off[r1] - s_off[r0];
     int slot;
     if (2 * n > target) slot = atomicAdd(counters + kCntItems, 1);
     else slot = cap - 1 - atomicAdd(counters + kCntItemsBack, 1);
-    if (slot >= 0 && slot < cap) items[slot] = Item{s, prev, next, n};
-    prev = next;
-    prev_off = next_off;
+    if (slot >= 0 && slot < cap) items[slot] = Item{s, rb + r0, rb + r1, n};
   }
 }
 
@@ -229,8 +234,10 @@ int bin_launch(const BinArgs& a, cudaStream_t st) {
   const int threads = 256;
   const long long want = (a.nvis + threads - 1) / threads;
   const int blocks = static_cast<int>(want < a.max_blocks ? (want > 0 ? want : 1) : a.max_blocks);
-  k_bin_count<<<blocks, threads, 0, st>>>(a.uv, a.nvis, a.scale2, a.W, a.N, a.n_strips, a.pos, a.rank, a.hist,
-                                          a.bad_list, a.dup_list, a.counters);
+  const long long want_c = (a.nvis + threads * kCountIlp - 1) / (threads * kCountIlp);
+  const int blocks_c = static_cast<int>(want_c < a.max_blocks ? (want_c > 0 ? want_c : 1) : a.max_blocks);
+  k_bin_count<<<blocks_c, threads, 0, st>>>(a.uv, a.nvis, a.scale2, a.W, a.N, a.n_strips, a.pos, a.rank, a.hist,
+                                          a.counters);
   const int nchunks = static_cast<int>((L + kScanChunk - 1) / kScanChunk);
   k_scan_partials<<<nchunks, kScanThreads, 0, st>>>(a.hist, L, a.partial);
   k_scan_top<<<1, 1024, 0, st>>>(a.partial, nchunks);
@@ -238,7 +245,8 @@ int bin_launch(const BinArgs& a, cudaStream_t st) {
   k_bin_scatter<<<blocks, threads, 0, st>>>(a.pos, a.rank, a.nvis, a.W, a.N, a.n_strips, a.offsets, a.recs);
   const int nblk = (a.N + a.rows_per_block - 1) / a.rows_per_block;
   const int ntask = a.n_strips * nblk;
-  k_make_items<<<(ntask + 127) / 128, 128, 0, st>>>(a.offsets, a.N, a.n_strips, a.rows_per_block, a.item_target,
+  if (a.rows_per_block > kMaxRowsPerBlock) return -1;
+  k_make_items<<<ntask, 128, 0, st>>>(a.offsets, a.N, a.n_strips, a.rows_per_block, a.item_target,
                                                    a.items, a.counters, a.item_cap);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

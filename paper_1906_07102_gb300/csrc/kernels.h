@@ -12,9 +12,9 @@ struct Item;
 
 // counters[] slots (device ints, reset by bin_launch)
 enum {
-  kCntBad = 0,         // dropped positions (bad_list length)
+  kCntBad = 0,         // dropped positions
   kCntItems = 1,       // items placed from the front (heavy)
-  kCntSecondary = 2,   // visibilities with a second-strip record (dup_list length)
+  kCntSecondary = 2,   // unused
   kCntItemsBack = 3,   // items placed from the back (light)
   kCntGridWork = 4,    // work counter of the gridding sweep
   kCntDegridWork = 5,  // work counter of the degridding sweep
@@ -34,8 +34,6 @@ struct BinArgs {
   int2* rank;      // max_vis: rank of the record(s) in their buckets
   int* partial;    // scan chunk sums
   Rec* recs;       // 2 * max_vis
-  int* dup_list;   // max_vis
-  int* bad_list;   // max_vis
   Item* items;     // item_cap
   int* counters;   // 8
 };
@@ -67,8 +65,7 @@ struct SweepArgs {
   const void* grid_in;
   void* vis_out;
   void* dpart;        // max_vis complex (secondary partial sums)
-  const int* dup_list;
-  const int* bad_list;
+  const VisPos* pos;  // per visibility support start (x0 < 0: dropped)
   long long nvis;
 };
 

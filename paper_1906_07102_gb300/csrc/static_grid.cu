@@ -42,9 +42,7 @@ constexpr size_t kOffHist = kOffRank + up256(sizeof(int2) * kMaxVis);
 constexpr size_t kOffOffsets = kOffHist + up256(sizeof(int) * kMaxBuckets);
 constexpr size_t kOffPartial = kOffOffsets + up256(sizeof(int) * (kMaxBuckets + 1));
 constexpr size_t kOffRecs = kOffPartial + up256(sizeof(int) * (kMaxBuckets / 4096 + 2));
-constexpr size_t kOffDup = kOffRecs + up256(sizeof(Rec) * 2 * kMaxVis);
-constexpr size_t kOffBad = kOffDup + up256(sizeof(int) * kMaxVis);
-constexpr size_t kOffItems = kOffBad + up256(sizeof(int) * kMaxVis);
+constexpr size_t kOffItems = kOffRecs + up256(sizeof(Rec) * 2 * kMaxVis);
 constexpr size_t kOffCounters = kOffItems + up256(sizeof(Item) * kMaxItems);
 constexpr size_t kOffSpill = kOffCounters + up256(sizeof(int) * kNumCounters);
 constexpr size_t kScratchBytes = kOffSpill + up256(sizeof(float2) * kMaxItems * kMaxRing * kStrip);
@@ -148,8 +146,6 @@ extern "C" int lmg_grid_static(const lmg_table* t, int64_t n_image, double pixel
   b.offsets = reinterpret_cast<int*>(base + kOffOffsets);
   b.partial = reinterpret_cast<int*>(base + kOffPartial);
   b.recs = reinterpret_cast<Rec*>(base + kOffRecs);
-  b.dup_list = reinterpret_cast<int*>(base + kOffDup);
-  b.bad_list = reinterpret_cast<int*>(base + kOffBad);
   b.items = reinterpret_cast<Item*>(base + kOffItems);
   b.counters = reinterpret_cast<int*>(base + kOffCounters);
   if (bin_launch(b, st) != 0) return set_error(LMG_ECUDA, std::string("binning launch: ") + cudaGetErrorString(cudaGetLastError()));

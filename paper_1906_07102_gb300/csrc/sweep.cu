@@ -498,26 +498,24 @@ __global__ void __launch_bounds__(kThreads, min_blocks<W, R>()) k_degrid_sweep(c
 }
 
 // Adds the partial sums of secondary records (supports crossing a strip boundary) and
-// zeroes the outputs of dropped positions.
+// zeroes the outputs of dropped positions; one pass over the visibilities' positions.
 template <typename R>
-__global__ void k_degrid_fixup(const int* __restrict__ dup_list, const int* __restrict__ bad_list,
-                               const int* __restrict__ counters, const typename Cplx<R>::T* __restrict__ dpart,
-                               typename Cplx<R>::T* __restrict__ out) {
-  const int n_dup = counters[kCntSecondary], n_bad = counters[kCntBad];
-  const int stride = gridDim.x * blockDim.x;
-  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n_dup + n_bad; m += stride) {
-    if (m < n_dup) {
-      const int k = dup_list[m];
+__global__ void k_degrid_fixup(const VisPos* __restrict__ pos, long long nvis, int W,
+                               const typename Cplx<R>::T* __restrict__ dpart, typename Cplx<R>::T* __restrict__ out) {
+  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+  for (long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; k < nvis; k += stride) {
+    const int x0 = pos[k].x0;
+    if (x0 < 0) {
+      typename Cplx<R>::T z;
+      z.x = 0;
+      z.y = 0;
+      out[k] = z;
+    } else if ((x0 % kStrip) + W > kStrip) {
       auto v = out[k];
       const auto p = dpart[k];
       v.x += p.x;
       v.y += p.y;
       out[k] = v;
-    } else {
-      typename Cplx<R>::T z;
-      z.x = 0;
-      z.y = 0;
-      out[bad_list[m - n_dup]] = z;
     }
   }
 }
@@ -634,11 +632,11 @@ int degrid_launch(const SweepArgs& a, cudaStream_t st) {
   void* params[] = {&args};
   if (cudaLaunchKernel(k, dim3(a.grid_blocks), dim3(32 * a.warps), params, smem, st) != cudaSuccess) return -1;
   if (a.dtype) {
-    k_degrid_fixup<double><<<2 * 152, 256, 0, st>>>(a.dup_list, a.bad_list, a.counters,
+    k_degrid_fixup<double><<<8 * 152, 256, 0, st>>>(a.pos, a.nvis, a.W,
                                                     static_cast<const double2*>(a.dpart),
                                                     static_cast<double2*>(a.vis_out));
   } else {
-    k_degrid_fixup<float><<<2 * 152, 256, 0, st>>>(a.dup_list, a.bad_list, a.counters,
+    k_degrid_fixup<float><<<8 * 152, 256, 0, st>>>(a.pos, a.nvis, a.W,
                                                    static_cast<const float2*>(a.dpart),
                                                    static_cast<float2*>(a.vis_out));
   }
