@@ -1,0 +1,144 @@
+"""C ABI of liblmg on the host (no GPU needed): every declared entry point is exported, the
+host-side table builder agrees with the oracle, and argument errors are reported.
+No call here launches a kernel."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import design as D
+from oracle import imaging as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lmg.h")
+
+
+@pytest.fixture(scope="module")
+def lmg():
+    from paper_1906_07102_gb300 import build, lmg as L
+    if not os.path.exists(L.LIB_PATH):
+        build.build()
+    L.lib()
+    return L
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lmg_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_function_is_exported_and_bound(lmg):
+    names = declared_functions()
+    assert len(names) >= 20
+    raw = ctypes.CDLL(lmg.LIB_PATH)
+    for n in names:
+        assert hasattr(raw, n), n
+        assert n in lmg.EXPORTED, n
+    assert lmg.lib().lmg_version().decode().startswith("lmg")
+
+
+@pytest.mark.parametrize("args,msg", [
+    ((0, 0.5, 100, 1, 0), "W must be"), ((17, 0.5, 100, 1, 0), "W must be"),
+    ((7, 0.0, 100, 1, 0), "x0 must be"), ((7, 1.5, 100, 1, 0), "x0 must be"),
+    ((7, 0.5, 1, 1, 0), "oversample"), ((7, 0.5, 100, 2, 0), "interp"), ((7, 0.5, 100, 1, 5), "correction")])
+def test_table_argument_errors(lmg, args, msg):
+    h = ctypes.c_void_p()
+    rc = lmg.lib().lmg_kernel_table(*args, ctypes.byref(h))
+    assert rc == -1 and not h.value
+    assert msg in lmg.lib().lmg_last_error().decode()
+
+
+def test_null_outputs_are_rejected(lmg):
+    L = lmg.lib()
+    assert L.lmg_kernel_table(7, 0.5, 100, 1, 0, None) == -1
+    assert L.lmg_table_export(None, None, 0, None, 0, None, None) == -1
+    assert L.lmg_plan_bin(None, None, 0, None) == -1
+    assert L.lmg_grid(None, None, None, 0, None, None) == -1
+
+
+@pytest.mark.parametrize("W,Ms,interp", [(3, 100, "nearest"), (5, 200, "linear")])
+def test_library_table_matches_oracle(lmg, W, Ms, interp):
+    """The library's C++ optimiser and the oracle's scipy one reach the same optimum; the
+    optimum of E is determined to about 1e-9 in float64 (flat directions of h)."""
+    t = lmg.Table(W, 0.5, Ms, interp)
+    C, h, E, info = t.export()
+    ho = D.least_misfit_h(W, 0.25)
+    Co = D.lm_table(ho, W, 0.25, Ms)
+    assert info[0] == W and info[1] == Ms and info[2] == 32
+    assert abs(E - D.design_E(ho, W, 0.25)) <= 1e-6 * E
+    assert np.abs(C - Co).max() <= 1e-6 * np.abs(Co).max()
+    assert np.abs(h - ho).max() <= 1e-5
+    n_img, N = 64, 128
+    hv = t.correction(n_img)
+    hvo = D.correction_factors(Co, Ms, 1 if interp == "linear" else 0, W, I.pixel_coords(n_img, N))
+    np.testing.assert_allclose(hv, hvo, rtol=1e-6)
+
+
+def test_w7_library_table_reaches_paper_level(lmg):
+    """W = 7, x0 = 0.25 (API 0.5): E of order 1e-14 (Section 2.2) from the library's own
+    optimiser; the table is mirror-symmetric (Section 5.2)."""
+    t = lmg.Table(7, 0.5, 1000, "linear")
+    C, h, E, _ = t.export()
+    assert 1e-16 < E < 3e-14
+    assert np.all(np.diff(h) > 0)
+    assert np.abs(C[::-1, ::-1] - C).max() < 1e-10 * np.abs(C).max()
+
+
+def test_table_from_values_round_trip(lmg):
+    vals = np.random.default_rng(0).random((65, 4))
+    t = lmg.Table(4, 0.5, 64, "linear", values=vals)
+    C, h, E, _ = t.export()
+    np.testing.assert_array_equal(C, vals)
+    assert np.isnan(E) and np.all(h == 0)
+    bad = vals.copy()
+    bad[3, 2] = np.nan
+    with pytest.raises(lmg.LmgError, match="finite"):
+        lmg.Table(4, 0.5, 64, "linear", values=bad)
+
+
+def test_correction_single_precision_rounding(lmg):
+    """The float32 path's correction factors use the table rounded to float32."""
+    t = lmg.Table(7, 0.5, 1000, "linear")
+    h64 = t.correction(128)
+    h32 = t.correction(128, single_precision=True)
+    assert 0 < np.abs(h64 - h32).max() < 1e-6 * np.abs(h64).max()
+
+
+def test_correction_rejects_non_even_grid(lmg):
+    t = lmg.Table(5, 0.5, 100, "linear")
+    out = np.empty(63)
+    assert lmg.lib().lmg_correction_export(t._h, 63, 0, out.ctypes.data_as(ctypes.c_void_p)) == -1
+
+
+def test_static_grid_validates_before_touching_the_device(lmg):
+    t = lmg.Table(7, 0.5, 1000, "linear")
+    L = lmg.lib()
+    rc = L.lmg_grid_static(t._h, 512, 1e-3, None, lmg.STATIC_MAX_VIS + 1, None, None, ctypes.c_void_p(16), None)
+    assert rc == -1 and "lmg_grid_static" in L.lmg_last_error().decode()
+    rc = L.lmg_grid_static(t._h, 4 * lmg.STATIC_MAX_N, 1e-3, None, 0, None, None, ctypes.c_void_p(16), None)
+    assert rc == -1 and "lmg_grid_static" in L.lmg_last_error().decode()
+
+
+def test_plan_creation_without_a_device_reports_an_error(lmg):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    t = lmg.Table(5, 0.5, 100, "linear")
+    h = ctypes.c_void_p()
+    rc = lmg.lib().lmg_plan_create(t._h, 64, 1e-3, 100, 0, ctypes.byref(h))
+    assert rc < 0 and not h.value
+    assert lmg.lib().lmg_last_error().decode() != ""
+
+
+def test_plan_argument_errors_precede_device_work(lmg):
+    t = lmg.Table(5, 0.5, 100, "linear")
+    h = ctypes.c_void_p()
+    L = lmg.lib()
+    for n_img, scale, maxv, dtype, msg in ((63, 1e-3, 10, 0, "n_image"), (64, 0.0, 10, 0, "pixel_scale"),
+                                           (64, 1e-3, 0, 0, "max_vis"), (64, 1e-3, 10, 3, "dtype"),
+                                           (40, 1e-3, 10, 0, "multiple of 32")):
+        assert L.lmg_plan_create(t._h, n_img, scale, maxv, dtype, ctypes.byref(h)) == -1
+        assert msg in L.lmg_last_error().decode()
