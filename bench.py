@@ -7,6 +7,16 @@ degrid to predicted visibilities. Workload: 64-antenna Earth-rotation tracks (6 
 W = 7, linear table at M_s = 1000, complex64.
 
 Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle instead.
+
+Two further workloads print their own line (not the headline):
+  --workload channels  96 frequency channels of uneven visibility counts (log-uniform in
+                       1e5-2e6), grid sizes drawn from {1024^2, 2048^2, 4096^2} and W from
+                       {4, 6, 8}: gridding + degridding as a tuned, graph-captured batch
+                       (one persistent sweep per W) against 96 sequential single-plan calls.
+  --workload autograd  differentiable imaging, L = ||P I - V||^2 with 49.5e6 visibilities
+                       (64 channels x 384 samples over 0.95-1.05 GHz), 4096^2 grid, W = 8:
+                       forward + backward with all channels in one plan against one plan
+                       per channel.
 """
 import argparse
 import hashlib
@@ -36,6 +46,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="tracks", choices=["tracks", "channels", "autograd"])
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=0,
@@ -398,10 +409,259 @@ def run_native(args):
         torch.distributed.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------------------
+# further workloads: batched channels, differentiable imaging
+# ---------------------------------------------------------------------------------------
+CHANNELS = dict(n_chan=96, n_ant=64, hours=6.0, f_lo=0.95e9, f_hi=1.05e9, nv_lo=1e5, nv_hi=2e6,
+                sizes=(1024, 2048, 4096), Ws=(4, 6, 8), x0=0.5, oversample=1000, n_src=4, noise_sigma=0.1)
+CHANNELS_NAME = ("96 frequency channels (0.95-1.05 GHz) of 64-antenna 6 h tracks, visibility counts log-uniform "
+                 "in 1e5-2e6, grids drawn from {1024^2, 2048^2, 4096^2}, W from {4, 6, 8}, x0 = 0.5, linear "
+                 "tables M_s = 1000, complex64, 4 point sources + noise")
+
+
+def make_channels():
+    from paper_1906_07102_gb300 import synthetic as S
+    c = CHANNELS
+    g = np.random.default_rng(2024)
+    nvs = np.exp(g.uniform(np.log(c["nv_lo"]), np.log(c["nv_hi"]), c["n_chan"])).astype(np.int64)
+    Ns = g.choice(c["sizes"], c["n_chan"])
+    Ws = g.choice(c["Ws"], c["n_chan"])
+    freqs = np.linspace(c["f_lo"], c["f_hi"], c["n_chan"])
+    nbl = c["n_ant"] * (c["n_ant"] - 1) // 2
+    chans = []
+    for k in range(c["n_chan"]):
+        n_times = int(-(-nvs[k] // nbl))
+        uv = S.array_tracks(n_ant=c["n_ant"], hours=c["hours"], n_times=n_times, freqs_hz=(freqs[k],), seed=0)
+        uv = np.ascontiguousarray(uv[:nvs[k]])
+        dl = S.pixel_scale_for(uv)
+        n_img = int(Ns[k]) // 2
+        l, m, f = S.point_source_sky(c["n_src"], 0.45 * n_img * dl, seed=k)
+        vis = S.visibilities(uv, l, m, f, noise_sigma=c["noise_sigma"], seed=k).astype(np.complex64)
+        chans.append(dict(uv=uv, dl=dl, vis=vis, N=int(Ns[k]), n_img=n_img, W=int(Ws[k])))
+    return chans
+
+
+def _events_ms(step, steps, flush, stream, torch):
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        starts[k].record(stream)
+        step()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    return float(np.mean([s.elapsed_time(e) for s, e in zip(starts, ends)]))
+
+
+def run_channels(args):
+    """Batched channels: tuned, graph-captured batch against sequential single plans."""
+    import torch
+    from paper_1906_07102_gb300 import lmg
+    torch.cuda.set_device(0)
+    c = CHANNELS
+    chans = make_channels()
+    nv_total = int(sum(ch["uv"].shape[0] for ch in chans))
+    dev = torch.device("cuda", 0)
+    tabs = {W: lmg.Table(W, c["x0"], c["oversample"], "linear") for W in c["Ws"]}
+    uvs = [torch.from_numpy(ch["uv"]).to(dev) for ch in chans]
+    vis = [torch.from_numpy(ch["vis"]).to(dev) for ch in chans]
+    batch = lmg.Batch([tabs[ch["W"]] for ch in chans], [ch["n_img"] for ch in chans], [ch["dl"] for ch in chans],
+                      [ch["uv"].shape[0] for ch in chans])
+    batch.bin(uvs)
+    chosen = batch.tune(vis)
+    grids = [torch.empty((ch["N"], ch["N"]), dtype=torch.complex64, device=dev) for ch in chans]
+    vout = [torch.empty_like(v) for v in vis]
+    plans = []
+    for ch, u in zip(chans, uvs):
+        p = lmg.Plan(tabs[ch["W"]], ch["n_img"], ch["dl"], ch["uv"].shape[0], "c64")
+        p.bin(u)
+        plans.append(p)
+    grids_s = [torch.empty_like(g) for g in grids]
+    vout_s = [torch.empty_like(v) for v in vis]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def batched():
+        batch.grid(vis, out=grids)
+        batch.degrid(grids, out=vout)
+
+    def sequential():
+        for p, v, g, o in zip(plans, vis, grids_s, vout_s):
+            p.grid(v, out=g)
+            p.degrid(g, out=o)
+
+    for _ in range(max(3, args.warmup)):
+        batched()
+        sequential()
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    clocks.start()
+    t_wall = time.perf_counter()
+    ms_b = _events_ms(batched, args.steps, flush, stream, torch)
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    ms_s = _events_ms(sequential, args.steps, flush, stream, torch)
+    # same accuracy: the batched outputs against the sequential ones
+    batched()
+    sequential()
+    torch.cuda.synchronize()
+    d_grid = max(float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)) for a, b in zip(grids, grids_s))
+    d_vis = max(float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)) for a, b in zip(vout, vout_s))
+    # end to end: visibilities in from pinned host memory, predictions out, every step
+    vis_h = [v.cpu().pin_memory() for v in vis]
+    out_h = [torch.empty(v.shape, dtype=v.dtype).pin_memory() for v in vis]
+
+    def e2e():
+        for d, h in zip(vis, vis_h):
+            d.copy_(h, non_blocking=True)
+        batched()
+        for h, d in zip(out_h, vout):
+            h.copy_(d, non_blocking=True)
+
+    e2e()
+    torch.cuda.synchronize()
+    ms_e = _events_ms(e2e, max(3, min(args.steps, 10)), flush, stream, torch)
+    sizes = [ch["N"] for ch in chans]
+    algo = sum(ch["uv"].shape[0] * 48 + 2 * ch["N"] ** 2 * 8 for ch in chans)
+    peak, src = measured_peak_hbm()
+    achieved = algo / (ms_b * 1e-3) / 1e9
+    n_w = len(set(ch["W"] for ch in chans))
+    line = {"metric": "Mvis/s grid+degrid, 96 channels batched (graph-captured, tuned) vs 96 sequential plain calls",
+            "value": nv_total / (ms_b * 1e-3) / 1e6, "unit": "Mvis/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": CHANNELS_NAME, "nvis": nv_total, "channels": len(chans),
+                       "grids": {str(n): sizes.count(n) for n in sorted(set(sizes))},
+                       "W": {str(w): sum(ch["W"] == w for ch in chans) for w in sorted(set(ch["W"] for ch in chans))},
+                       "tuned": {"rows_per_bin": chosen[0], "records_per_item": chosen[1], "warps": chosen[2],
+                                 "tables_in_shared_memory": bool(chosen[3])},
+                       "parallelism": "single GPU",
+                       "l2": "flushed before every timed step (256 MB write, outside the step's events)"},
+            "sequential": {"value": nv_total / (ms_s * 1e-3) / 1e6, "ms_per_step": ms_s,
+                           "form": "96 x (lmg_grid + lmg_degrid), one plan per channel"},
+            "speedup_vs_sequential": ms_s / ms_b,
+            "batched_vs_sequential_rel_diff": {"grid_max_rel_l2": d_grid, "vis_max_rel_l2": d_vis},
+            "roofline": {"kernel": "batched step (sweeps + spill + fix-up, all channels)", "bound": "hbm",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "algorithmic_bytes": algo,
+                         "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)"},
+            "clocks": clk, "timed_wall_s": t_wall,
+            "e2e": {"value": nv_total / (ms_e * 1e-3) / 1e6, "unit": "Mvis/s",
+                    "h2d_bytes_per_step": nv_total * 8, "d2h_bytes_per_step": nv_total * 8},
+            "gpu_launches": 4 * n_w * args.steps}
+    print(json.dumps(line), flush=True)
+
+
+AUTOGRAD = dict(n_ant=64, hours=6.0, n_times=384, n_chan=64, f_lo=0.95e9, f_hi=1.05e9, N=4096, n_image=2048,
+                x0=0.5, W=8, oversample=1000, n_src=4, noise_sigma=0.1)
+
+
+def run_autograd(args):
+    """Differentiable imaging: forward + backward with all channels in one plan against one
+    plan per channel (same loss, same gradient)."""
+    import torch
+    from paper_1906_07102_gb300 import lmg
+    from paper_1906_07102_gb300 import synthetic as S
+    torch.cuda.set_device(0)
+    a = AUTOGRAD
+    freqs = np.linspace(a["f_lo"], a["f_hi"], a["n_chan"])
+    uv = S.array_tracks(n_ant=a["n_ant"], hours=a["hours"], n_times=a["n_times"], freqs_hz=freqs, seed=0)
+    dl = S.pixel_scale_for(uv)
+    l, m, f = S.point_source_sky(a["n_src"], 0.45 * a["n_image"] * dl, seed=0)
+    V = S.visibilities(uv, l, m, f, noise_sigma=a["noise_sigma"], seed=0).astype(np.complex64)
+    image = S.gaussian_blob_image(a["n_image"], 64, seed=0).astype(np.float32)
+    nv = uv.shape[0]
+    per = nv // a["n_chan"]
+    dev = torch.device("cuda", 0)
+    tab = lmg.Table(a["W"], a["x0"], a["oversample"], "linear")
+    uv_d = torch.from_numpy(uv).to(dev)
+    V_d = torch.from_numpy(V).to(dev)
+    img_d = torch.from_numpy(image).to(dev)
+    one = lmg.Plan(tab, a["n_image"], dl, nv, "c64")
+    one.bin(uv_d)
+    plans = []
+    for k in range(a["n_chan"]):
+        p = lmg.Plan(tab, a["n_image"], dl, per, "c64")
+        p.bin(uv_d[k * per:(k + 1) * per])
+        plans.append(p)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    grads = {}
+
+    def batched():
+        x = img_d.clone().requires_grad_(True)
+        r = lmg.predict(x, one) - V_d
+        (r.real.double() ** 2 + r.imag.double() ** 2).sum().backward()
+        grads["batched"] = x.grad
+
+    def per_channel():
+        x = img_d.clone().requires_grad_(True)
+        L = 0
+        for k, p in enumerate(plans):
+            r = lmg.predict(x, p) - V_d[k * per:(k + 1) * per]
+            L = L + (r.real.double() ** 2 + r.imag.double() ** 2).sum()
+        L.backward()
+        grads["per_channel"] = x.grad
+
+    for _ in range(max(3, args.warmup)):
+        batched()
+        per_channel()
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    clocks.start()
+    ms_b = _events_ms(batched, args.steps, flush, stream, torch)
+    clk = clocks.stop()
+    ms_p = _events_ms(per_channel, args.steps, flush, stream, torch)
+    gb, gp = grads["batched"].double(), grads["per_channel"].double()
+    diff = float(torch.linalg.vector_norm(gb - gp) / torch.linalg.vector_norm(gp))
+    # end to end: image and visibilities in from pinned memory, gradient out
+    img_h = torch.from_numpy(image).pin_memory()
+    V_h = torch.from_numpy(V).pin_memory()
+    g_h = torch.empty(image.shape, dtype=torch.float32).pin_memory()
+
+    def e2e():
+        img_d.copy_(img_h, non_blocking=True)
+        V_d.copy_(V_h, non_blocking=True)
+        batched()
+        g_h.copy_(grads["batched"], non_blocking=True)
+
+    e2e()
+    torch.cuda.synchronize()
+    ms_e = _events_ms(e2e, max(3, min(args.steps, 10)), flush, stream, torch)
+    algo = nv * 48 + 2 * a["N"] ** 2 * 8
+    peak, src = measured_peak_hbm()
+    achieved = algo / (ms_b * 1e-3) / 1e9
+    line = {"metric": "Mvis/s forward+backward of ||P I - V||^2 (degrid + grid), all channels in one plan vs one "
+                      "plan per channel",
+            "value": nv / (ms_b * 1e-3) / 1e6, "unit": "Mvis/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "64-antenna tracks, 384 samples x 64 channels (0.95-1.05 GHz), 49.5e6 vis, "
+                                   "4096^2 grid, 2048^2 float32 Gaussian-blob image, W=8, M_s=1000",
+                       "nvis": nv, "parallelism": "single GPU",
+                       "l2": "flushed before every timed step (256 MB write, outside the step's events)"},
+            "per_channel": {"value": nv / (ms_p * 1e-3) / 1e6, "ms_per_step": ms_p,
+                            "form": "64 plans, loss summed over channels"},
+            "speedup_vs_per_channel": ms_p / ms_b,
+            "gradient_rel_diff_vs_per_channel": diff,
+            "roofline": {"kernel": "forward + backward step", "bound": "hbm", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": None, "algorithmic_bytes": algo,
+                         "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)"},
+            "clocks": clk,
+            "e2e": {"value": nv / (ms_e * 1e-3) / 1e6, "unit": "Mvis/s",
+                    "h2d_bytes_per_step": image.nbytes + V.nbytes, "d2h_bytes_per_step": image.nbytes},
+            "gpu_launches": 6 * args.steps}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "channels":
+        run_channels(args)
+    elif args.workload == "autograd":
+        run_autograd(args)
     else:
         run_native(args)
 

@@ -69,6 +69,7 @@ enum { LMG_FFT_IMAGE = +1, LMG_FFT_MODEL = -1 };
 
 typedef struct lmg_table lmg_table; /* least-misfit function (host float64) */
 typedef struct lmg_plan lmg_plan;   /* device state for one (table, n_image, x0, pixel_scale) */
+typedef struct lmg_batch lmg_batch; /* many independent channels gridded together */
 
 /* lmg_kernel_table -- build the least-misfit gridding function and its look-up table.
  *
@@ -214,6 +215,67 @@ void* lmg_work_grid(lmg_plan* p);
 #define LMG_STATIC_MAX_OVERSAMPLE 4096
 int lmg_grid_static(const lmg_table* t, int64_t n_image, double pixel_scale, const double* uv,
                     int64_t nvis, const void* vis, const void* weights, void* grid, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Multi-channel batches. Channels (for example frequency channels, each with its own uv
+ * set in wavelengths) are independent problems of Sections 2-4, each with its own table
+ * (so its own W), grid size and pixel scale. A batch runs them together: every channel is
+ * binned as by lmg_plan_bin, then the sweeps of all channels with the same W run as ONE
+ * persistent kernel launch, whose warps take work items of every such channel from one
+ * counter. FFTs run as one batched cuFFT plan per distinct grid size. The launch sequence
+ * of each operation is captured once into a CUDA graph on the batch's own stream (ordered
+ * after and before the caller's stream by events) and replayed while the caller passes the
+ * same buffers; new buffers trigger a new capture.
+ * Complex64 only. Arrays of per-channel arguments are HOST arrays of length n_chan whose
+ * entries are DEVICE pointers (complex64 vis/grids/images, float32 weights, float64 uv).
+ * The batch copies what it needs from the arrays during the call.
+ * --------------------------------------------------------------------------------------- */
+#define LMG_BATCH_MAX_CHANNELS 1024
+
+/* lmg_batch_create -- per channel c: table tables[c] (not owned; must outlive the batch),
+ * image size n_image[c], pixel scale pixel_scale[c] (radians) and capacity max_vis[c].
+ * Same argument rules as lmg_plan_create for each channel; 1 <= n_chan <=
+ * LMG_BATCH_MAX_CHANNELS. Allocates every channel's binning buffers, one work grid per
+ * channel (contiguous per grid size) and one batched FFT plan per grid size. */
+int lmg_batch_create(int n_chan, const lmg_table* const* tables, const int64_t* n_image,
+                     const double* pixel_scale, const int64_t* max_vis, lmg_batch** out);
+int lmg_batch_free(lmg_batch* b);
+
+/* lmg_batch_bin -- bins channel c's uv[c] (device float64 [nvis[c]][2], 16-byte aligned)
+ * for every c; uv[c] may be NULL when nvis[c] == 0. Invalidates captured graphs. */
+int lmg_batch_bin(lmg_batch* b, const double* const* uv, const int64_t* nvis, void* stream);
+
+/* lmg_batch_grid -- grid[c] = gridded vis[c] (x weights[c]) for every channel, as lmg_grid
+ * with plain accumulation. weights may be NULL (all unweighted) or hold NULL entries. */
+int lmg_batch_grid(lmg_batch* b, const void* const* vis, const void* const* weights, void* const* grid,
+                   void* stream);
+
+/* lmg_batch_degrid -- vis_out[c] = degridded grid[c] for every channel, as lmg_degrid. */
+int lmg_batch_degrid(lmg_batch* b, const void* const* grid, void* const* vis_out, void* stream);
+
+/* lmg_batch_dirty_image -- image[c] ([n_image[c]]^2) = dirty image of vis[c], as
+ * lmg_dirty_image (plain accumulation) for every channel, through the batch's work grids. */
+int lmg_batch_dirty_image(lmg_batch* b, const void* const* vis, const void* const* weights,
+                          void* const* image, void* stream);
+
+/* lmg_batch_predict_vis -- vis_out[c] = predicted visibilities of image[c], as
+ * lmg_predict_vis for every channel. */
+int lmg_batch_predict_vis(lmg_batch* b, const void* const* image, void* const* vis_out, void* stream);
+
+/* lmg_batch_tune -- autotuner. Times gridding plus degridding of the current binned uv
+ * sets with vis[c] (device complex64 [nvis[c]], used read-only) for each candidate of: rows
+ * per work item bin (64, 128, 256, 512), records per work item (256, 512, 1024, 2048), warps
+ * per CTA (4, 8) and table placement (shared or global memory, where the tables fit),
+ * keeps the fastest, re-bins every channel with it and writes it to chosen[4] (rows,
+ * records, warps, table in shared memory) when chosen is not NULL. Requires a prior
+ * lmg_batch_bin with the same uv (its pointers are reused for re-binning). Synchronises
+ * the stream; allocates and frees scratch output. Not capturable. */
+int lmg_batch_tune(lmg_batch* b, const void* const* vis, void* stream, int* chosen);
+
+/* lmg_batch_info -- out[0] channels, out[1] distinct W, out[2] distinct grid sizes,
+ * out[3] total visibilities binned, out[4] rows per bin, out[5] records per item,
+ * out[6] warps per CTA, out[7] graphs captured so far. */
+int lmg_batch_info(lmg_batch* b, int64_t* out);
 
 /* lmg_last_error -- message for the calling thread's most recent failure ("" if none). */
 const char* lmg_last_error(void);

@@ -22,46 +22,18 @@ int set_error(int status, const std::string& msg) {
   return status;
 }
 void clear_error() { g_error.clear(); }
+int cuda_error(cudaError_t e, const char* what) {
+  return set_error(LMG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
 }  // namespace lmg
 
 using namespace lmg;
 
-struct lmg_plan {
-  int W = 0, Ms = 0, interp = 1, dtype = 0, Wp = 0;
-  int64_t n_image = 0, N = 0;
-  double x0 = 0, pixel_scale = 0, scale2 = 0;
-  int n_strips = 0, rows_per_block = 256, item_target = 1024, item_cap = 0, nchunks = 0;
-  int64_t max_vis = 0, nvis = -1;
-  int device = 0, sms = 0;
-  int blocks_grid = 0, blocks_degrid = 0;
-  bool tab_smem_grid = false, tab_smem_degrid = false;
-  int warps_grid = 8, warps_degrid = 8;
-  size_t smem_grid = 0, smem_degrid = 0;
-  int blocks_grid_comp = 0;
-  void* d_table = nullptr;
-  void* d_h = nullptr;
-  VisPos* pos = nullptr;
-  int* hist = nullptr;
-  int* offsets = nullptr;
-  int2* rank = nullptr;
-  int* partial = nullptr;
-  Rec* recs = nullptr;
-  Item* items = nullptr;
-  int* counters = nullptr;
-  void* spill = nullptr;
-  void* dpart = nullptr;
-  void* work = nullptr;
-  cufftHandle fft = 0;
-  bool fft_ok = false;
-};
 
 namespace {
 
 const char* kVersion = "lmg 0.1 (sm_103a)";
 
-int cuda_fail(cudaError_t e, const char* what) {
-  return set_error(LMG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
-}
 
 bool check_table_args(int W, double x0, int Ms, int interp, int correction) {
   if (W < 1 || W > kMaxW) return set_error(LMG_EINVAL, "W must be in [1, 16]"), false;
@@ -86,6 +58,10 @@ template <typename T> int dalloc(T** p, size_t count, const char* what) {
   }
   return LMG_OK;
 }
+
+}  // namespace
+
+namespace lmg {
 
 void free_plan(lmg_plan* p) {
   if (!p) return;
@@ -116,6 +92,10 @@ SweepArgs sweep_args(const lmg_plan* p) {
   a.nvis = p->nvis;
   return a;
 }
+
+}  // namespace lmg
+
+namespace {
 
 int need_binned(const lmg_plan* p) {
   if (p->nvis < 0) return set_error(LMG_EINVAL, "plan has no binned positions (call lmg_plan_bin first)");
@@ -167,6 +147,154 @@ int do_fft(lmg_plan* p, int direction, void* g, cudaStream_t st) {
 }
 
 }  // namespace
+
+namespace lmg {
+
+int plan_create(const lmg_table* t, int64_t n_image, double pixel_scale, int64_t max_vis, int dtype,
+                const PlanOptions& opt, lmg_plan** out) {
+  if (!out) return set_error(LMG_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!t) return set_error(LMG_EINVAL, "table is NULL");
+  if (dtype != LMG_C64 && dtype != LMG_C128) return set_error(LMG_EINVAL, "dtype must be LMG_C64 or LMG_C128");
+  if (!(pixel_scale > 0.0) || !std::isfinite(pixel_scale)) return set_error(LMG_EINVAL, "pixel_scale must be > 0");
+  if (max_vis < 1 || max_vis > (int64_t(1) << 30)) return set_error(LMG_EINVAL, "max_vis must be in [1, 2^30]");
+  if (n_image < 2 || (n_image & 1)) return set_error(LMG_EINVAL, "n_image must be even and >= 2");
+  const double Nd = double(n_image) / t->x0;
+  const int64_t N = int64_t(std::llround(Nd));
+  if (std::fabs(Nd - double(N)) > 1e-9 * Nd || (N & 1))
+    return set_error(LMG_EINVAL, "n_image / x0 must be an even integer");
+  if (N < 64 || N % kStrip != 0 || N > 65536)
+    return set_error(LMG_EINVAL, "grid size N = n_image / x0 must be a multiple of 32 in [64, 65536]");
+  if (N < 2 * t->W) return set_error(LMG_EINVAL, "grid too small for the support width");
+
+  lmg_plan* p = new (std::nothrow) lmg_plan;
+  if (!p) return set_error(LMG_ENOMEM, "host allocation failed");
+  p->W = t->W;
+  p->Ms = t->Ms;
+  p->interp = t->interp;
+  p->dtype = dtype;
+  p->n_image = n_image;
+  p->N = N;
+  p->x0 = t->x0;
+  p->pixel_scale = pixel_scale;
+  p->scale2 = double(N) * pixel_scale * 4294967296.0;
+  p->max_vis = max_vis;
+  p->n_strips = int(N / kStrip);
+  const size_t rs = dtype == LMG_C128 ? 8 : 4;
+  p->Wp = dtype == LMG_C128 ? ((p->W + 1) & ~1) : ((p->W + 3) & ~3);
+  const int nblk = int((N + opt.min_rows_per_block - 1) / opt.min_rows_per_block);
+  p->item_cap = p->n_strips * nblk + int((2 * max_vis) / opt.min_item_target) + 2;
+  const long long L = (long long)p->n_strips * N;
+  p->nchunks = bin_scan_chunks(L);
+
+  int rc;
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e != cudaSuccess) {
+    delete p;
+    return cuda_error(e, "cudaGetDevice");
+  }
+  e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
+  if (e != cudaSuccess) {
+    delete p;
+    return cuda_error(e, "cudaDeviceGetAttribute");
+  }
+  // Device table (rows padded to Wp) and correction factors in the plan's precision.
+  std::vector<double> hcorr(static_cast<size_t>(n_image));
+  correction_factors(t, n_image, N, dtype == LMG_C64, hcorr.data());
+  std::vector<unsigned char> tab_bytes(size_t(p->Ms + 1) * p->Wp * rs, 0), h_bytes(size_t(n_image) * rs);
+  for (int i = 0; i <= p->Ms; ++i)
+    for (int j = 0; j < p->W; ++j) {
+      const double v = t->C[size_t(i) * p->W + j];
+      if (rs == 8) reinterpret_cast<double*>(tab_bytes.data())[size_t(i) * p->Wp + j] = v;
+      else reinterpret_cast<float*>(tab_bytes.data())[size_t(i) * p->Wp + j] = float(v);
+    }
+  for (int64_t q = 0; q < n_image; ++q) {
+    if (rs == 8) reinterpret_cast<double*>(h_bytes.data())[q] = hcorr[size_t(q)];
+    else reinterpret_cast<float*>(h_bytes.data())[q] = float(hcorr[size_t(q)]);
+  }
+  const size_t c2 = 2 * rs;
+  if ((rc = dalloc(reinterpret_cast<unsigned char**>(&p->d_table), tab_bytes.size(), "table")) ||
+      (rc = dalloc(reinterpret_cast<unsigned char**>(&p->d_h), h_bytes.size(), "correction")) ||
+      (rc = dalloc(&p->pos, size_t(max_vis), "positions")) || (rc = dalloc(&p->hist, size_t(L), "histogram")) ||
+      (rc = dalloc(&p->offsets, size_t(L) + 1, "offsets")) || (rc = dalloc(&p->rank, size_t(max_vis), "ranks")) ||
+      (rc = dalloc(&p->partial, size_t(p->nchunks), "scan")) || (rc = dalloc(&p->recs, size_t(2 * max_vis), "records")) ||
+      (rc = dalloc(&p->items, size_t(p->item_cap), "items")) || (rc = dalloc(&p->counters, kNumCounters, "counters")) ||
+      (rc = dalloc(reinterpret_cast<unsigned char**>(&p->spill), size_t(p->item_cap) * ring_slots(p->W) * kStrip * c2, "spill")) ||
+      (rc = dalloc(reinterpret_cast<unsigned char**>(&p->dpart), size_t(max_vis) * c2, "partials")) ||
+      (opt.work_grid && (rc = dalloc(reinterpret_cast<unsigned char**>(&p->work), size_t(N) * size_t(N) * c2, "work grid")))) {
+    free_plan(p);
+    return rc;
+  }
+  if ((e = cudaMemcpy(p->d_table, tab_bytes.data(), tab_bytes.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(p->d_h, h_bytes.data(), h_bytes.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemset(p->counters, 0, kNumCounters * sizeof(int))) != cudaSuccess) {
+    free_plan(p);
+    return cuda_error(e, "plan upload");
+  }
+  // Launch shapes: warps per CTA and table placement that fit shared memory; persistent
+  // CTAs per SM from the occupancy calculator.
+  const size_t kSmemLimit = 200 * 1024;
+  int bps = 0;
+  if (sweep_config(p->W, dtype, p->Ms, false, kSmemLimit, &p->tab_smem_grid, &p->warps_grid) ||
+      sweep_config(p->W, dtype, p->Ms, true, kSmemLimit, &p->tab_smem_degrid, &p->warps_degrid)) {
+    free_plan(p);
+    return set_error(LMG_EUNSUPPORTED, "sweep shared memory does not fit for this W and dtype");
+  }
+  p->smem_grid = sweep_smem_bytes(p->W, dtype, p->Ms, p->tab_smem_grid, false, p->warps_grid);
+  p->smem_degrid = sweep_smem_bytes(p->W, dtype, p->Ms, p->tab_smem_degrid, true, p->warps_degrid);
+  for (int accum = 0; accum <= (dtype == LMG_C64 ? 1 : 0); ++accum) {
+    if (sweep_set_smem_limits(p->W, dtype, accum, p->smem_grid, false) ||
+        sweep_occupancy(p->W, dtype, accum, p->smem_grid, false, p->warps_grid, &bps)) {
+      free_plan(p);
+      return cuda_error(cudaGetLastError(), "sweep kernel attributes");
+    }
+    (accum ? p->blocks_grid_comp : p->blocks_grid) = p->sms * (bps > 0 ? bps : 1);
+  }
+  if (sweep_set_smem_limits(p->W, dtype, 0, p->smem_degrid, true) ||
+      sweep_occupancy(p->W, dtype, 0, p->smem_degrid, true, p->warps_degrid, &bps)) {
+    free_plan(p);
+    return cuda_error(cudaGetLastError(), "sweep kernel attributes");
+  }
+  p->blocks_degrid = p->sms * (bps > 0 ? bps : 1);
+  if (opt.fft) {
+    const cufftResult fr = cufftPlan2d(&p->fft, int(N), int(N), dtype == LMG_C128 ? CUFFT_Z2Z : CUFFT_C2C);
+    if (fr != CUFFT_SUCCESS) {
+      free_plan(p);
+      return set_error(fr == CUFFT_ALLOC_FAILED ? LMG_ENOMEM : LMG_ECUFFT,
+                       "cufftPlan2d failed (code " + std::to_string(int(fr)) + ")");
+    }
+    p->fft_ok = true;
+  }
+  *out = p;
+  return LMG_OK;
+}
+
+int plan_bin(lmg_plan* p, const double* uv, int64_t nvis, cudaStream_t st) {
+  BinArgs a{};
+  a.uv = uv;
+  a.nvis = nvis;
+  a.scale2 = p->scale2;
+  a.W = p->W;
+  a.N = int(p->N);
+  a.n_strips = p->n_strips;
+  a.rows_per_block = p->rows_per_block;
+  a.item_target = p->item_target;
+  a.item_cap = p->item_cap;
+  a.max_blocks = p->sms * 8;
+  a.pos = p->pos;
+  a.hist = p->hist;
+  a.offsets = p->offsets;
+  a.rank = p->rank;
+  a.partial = p->partial;
+  a.recs = p->recs;
+  a.items = p->items;
+  a.counters = p->counters;
+  const int rc = launch_status(bin_launch(a, st), "binning");
+  if (rc == LMG_OK) p->nvis = nvis;
+  return rc;
+}
+
+}  // namespace lmg
 
 extern "C" {
 
@@ -274,119 +402,7 @@ int lmg_correction_export(const lmg_table* t, int64_t n_image, int single_precis
 int lmg_plan_create(const lmg_table* t, int64_t n_image, double pixel_scale, int64_t max_vis, int dtype,
                     lmg_plan** out) {
   clear_error();
-  if (!out) return set_error(LMG_EINVAL, "out is NULL");
-  *out = nullptr;
-  if (!t) return set_error(LMG_EINVAL, "table is NULL");
-  if (dtype != LMG_C64 && dtype != LMG_C128) return set_error(LMG_EINVAL, "dtype must be LMG_C64 or LMG_C128");
-  if (!(pixel_scale > 0.0) || !std::isfinite(pixel_scale)) return set_error(LMG_EINVAL, "pixel_scale must be > 0");
-  if (max_vis < 1 || max_vis > (int64_t(1) << 30)) return set_error(LMG_EINVAL, "max_vis must be in [1, 2^30]");
-  if (n_image < 2 || (n_image & 1)) return set_error(LMG_EINVAL, "n_image must be even and >= 2");
-  const double Nd = double(n_image) / t->x0;
-  const int64_t N = int64_t(std::llround(Nd));
-  if (std::fabs(Nd - double(N)) > 1e-9 * Nd || (N & 1))
-    return set_error(LMG_EINVAL, "n_image / x0 must be an even integer");
-  if (N < 64 || N % kStrip != 0 || N > 65536)
-    return set_error(LMG_EINVAL, "grid size N = n_image / x0 must be a multiple of 32 in [64, 65536]");
-  if (N < 2 * t->W) return set_error(LMG_EINVAL, "grid too small for the support width");
-
-  lmg_plan* p = new (std::nothrow) lmg_plan;
-  if (!p) return set_error(LMG_ENOMEM, "host allocation failed");
-  p->W = t->W;
-  p->Ms = t->Ms;
-  p->interp = t->interp;
-  p->dtype = dtype;
-  p->n_image = n_image;
-  p->N = N;
-  p->x0 = t->x0;
-  p->pixel_scale = pixel_scale;
-  p->scale2 = double(N) * pixel_scale * 4294967296.0;
-  p->max_vis = max_vis;
-  p->n_strips = int(N / kStrip);
-  const size_t rs = dtype == LMG_C128 ? 8 : 4;
-  p->Wp = dtype == LMG_C128 ? ((p->W + 1) & ~1) : ((p->W + 3) & ~3);
-  const int nblk = int((N + p->rows_per_block - 1) / p->rows_per_block);
-  p->item_cap = p->n_strips * nblk + int((2 * max_vis) / p->item_target) + 2;
-  const long long L = (long long)p->n_strips * N;
-  p->nchunks = bin_scan_chunks(L);
-
-  int rc;
-  cudaError_t e = cudaGetDevice(&p->device);
-  if (e != cudaSuccess) {
-    delete p;
-    return cuda_fail(e, "cudaGetDevice");
-  }
-  e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
-  if (e != cudaSuccess) {
-    delete p;
-    return cuda_fail(e, "cudaDeviceGetAttribute");
-  }
-  // Device table (rows padded to Wp) and correction factors in the plan's precision.
-  std::vector<double> hcorr(static_cast<size_t>(n_image));
-  correction_factors(t, n_image, N, dtype == LMG_C64, hcorr.data());
-  std::vector<unsigned char> tab_bytes(size_t(p->Ms + 1) * p->Wp * rs, 0), h_bytes(size_t(n_image) * rs);
-  for (int i = 0; i <= p->Ms; ++i)
-    for (int j = 0; j < p->W; ++j) {
-      const double v = t->C[size_t(i) * p->W + j];
-      if (rs == 8) reinterpret_cast<double*>(tab_bytes.data())[size_t(i) * p->Wp + j] = v;
-      else reinterpret_cast<float*>(tab_bytes.data())[size_t(i) * p->Wp + j] = float(v);
-    }
-  for (int64_t q = 0; q < n_image; ++q) {
-    if (rs == 8) reinterpret_cast<double*>(h_bytes.data())[q] = hcorr[size_t(q)];
-    else reinterpret_cast<float*>(h_bytes.data())[q] = float(hcorr[size_t(q)]);
-  }
-  const size_t c2 = 2 * rs;
-  if ((rc = dalloc(reinterpret_cast<unsigned char**>(&p->d_table), tab_bytes.size(), "table")) ||
-      (rc = dalloc(reinterpret_cast<unsigned char**>(&p->d_h), h_bytes.size(), "correction")) ||
-      (rc = dalloc(&p->pos, size_t(max_vis), "positions")) || (rc = dalloc(&p->hist, size_t(L), "histogram")) ||
-      (rc = dalloc(&p->offsets, size_t(L) + 1, "offsets")) || (rc = dalloc(&p->rank, size_t(max_vis), "ranks")) ||
-      (rc = dalloc(&p->partial, size_t(p->nchunks), "scan")) || (rc = dalloc(&p->recs, size_t(2 * max_vis), "records")) ||
-      (rc = dalloc(&p->items, size_t(p->item_cap), "items")) || (rc = dalloc(&p->counters, kNumCounters, "counters")) ||
-      (rc = dalloc(reinterpret_cast<unsigned char**>(&p->spill), size_t(p->item_cap) * ring_slots(p->W) * kStrip * c2, "spill")) ||
-      (rc = dalloc(reinterpret_cast<unsigned char**>(&p->dpart), size_t(max_vis) * c2, "partials")) ||
-      (rc = dalloc(reinterpret_cast<unsigned char**>(&p->work), size_t(N) * size_t(N) * c2, "work grid"))) {
-    free_plan(p);
-    return rc;
-  }
-  if ((e = cudaMemcpy(p->d_table, tab_bytes.data(), tab_bytes.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(p->d_h, h_bytes.data(), h_bytes.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemset(p->counters, 0, kNumCounters * sizeof(int))) != cudaSuccess) {
-    free_plan(p);
-    return cuda_fail(e, "plan upload");
-  }
-  // Launch shapes: warps per CTA and table placement that fit shared memory; persistent
-  // CTAs per SM from the occupancy calculator.
-  const size_t kSmemLimit = 200 * 1024;
-  int bps = 0;
-  if (sweep_config(p->W, dtype, p->Ms, false, kSmemLimit, &p->tab_smem_grid, &p->warps_grid) ||
-      sweep_config(p->W, dtype, p->Ms, true, kSmemLimit, &p->tab_smem_degrid, &p->warps_degrid)) {
-    free_plan(p);
-    return set_error(LMG_EUNSUPPORTED, "sweep shared memory does not fit for this W and dtype");
-  }
-  p->smem_grid = sweep_smem_bytes(p->W, dtype, p->Ms, p->tab_smem_grid, false, p->warps_grid);
-  p->smem_degrid = sweep_smem_bytes(p->W, dtype, p->Ms, p->tab_smem_degrid, true, p->warps_degrid);
-  for (int accum = 0; accum <= (dtype == LMG_C64 ? 1 : 0); ++accum) {
-    if (sweep_set_smem_limits(p->W, dtype, accum, p->smem_grid, false) ||
-        sweep_occupancy(p->W, dtype, accum, p->smem_grid, false, p->warps_grid, &bps)) {
-      free_plan(p);
-      return cuda_fail(cudaGetLastError(), "sweep kernel attributes");
-    }
-    (accum ? p->blocks_grid_comp : p->blocks_grid) = p->sms * (bps > 0 ? bps : 1);
-  }
-  if (sweep_set_smem_limits(p->W, dtype, 0, p->smem_degrid, true) ||
-      sweep_occupancy(p->W, dtype, 0, p->smem_degrid, true, p->warps_degrid, &bps)) {
-    free_plan(p);
-    return cuda_fail(cudaGetLastError(), "sweep kernel attributes");
-  }
-  p->blocks_degrid = p->sms * (bps > 0 ? bps : 1);
-  const cufftResult fr = cufftPlan2d(&p->fft, int(N), int(N), dtype == LMG_C128 ? CUFFT_Z2Z : CUFFT_C2C);
-  if (fr != CUFFT_SUCCESS) {
-    free_plan(p);
-    return set_error(fr == CUFFT_ALLOC_FAILED ? LMG_ENOMEM : LMG_ECUFFT,
-                     "cufftPlan2d failed (code " + std::to_string(int(fr)) + ")");
-  }
-  p->fft_ok = true;
-  *out = p;
-  return LMG_OK;
+  return plan_create(t, n_image, pixel_scale, max_vis, dtype, PlanOptions{}, out);
 }
 
 int lmg_plan_free(lmg_plan* p) {
@@ -400,28 +416,7 @@ int lmg_plan_bin(lmg_plan* p, const double* uv, int64_t nvis, void* stream) {
   if (nvis < 0 || nvis > p->max_vis) return set_error(LMG_EINVAL, "nvis must be in [0, max_vis]");
   if (nvis > 0 && !uv) return set_error(LMG_EINVAL, "uv is NULL");
   if (reinterpret_cast<uintptr_t>(uv) % 16 != 0) return set_error(LMG_EINVAL, "uv must be 16-byte aligned");
-  BinArgs a{};
-  a.uv = uv;
-  a.nvis = nvis;
-  a.scale2 = p->scale2;
-  a.W = p->W;
-  a.N = int(p->N);
-  a.n_strips = p->n_strips;
-  a.rows_per_block = p->rows_per_block;
-  a.item_target = p->item_target;
-  a.item_cap = p->item_cap;
-  a.max_blocks = p->sms * 8;
-  a.pos = p->pos;
-  a.hist = p->hist;
-  a.offsets = p->offsets;
-  a.rank = p->rank;
-  a.partial = p->partial;
-  a.recs = p->recs;
-  a.items = p->items;
-  a.counters = p->counters;
-  const int rc = launch_status(bin_launch(a, static_cast<cudaStream_t>(stream)), "binning");
-  if (rc == LMG_OK) p->nvis = nvis;
-  return rc;
+  return plan_bin(p, uv, nvis, static_cast<cudaStream_t>(stream));
 }
 
 int lmg_plan_dropped(lmg_plan* p, int64_t* dropped, void* stream) {
@@ -430,7 +425,7 @@ int lmg_plan_dropped(lmg_plan* p, int64_t* dropped, void* stream) {
   int c[8];
   cudaError_t e = cudaMemcpyAsync(c, p->counters, sizeof(c), cudaMemcpyDeviceToHost, static_cast<cudaStream_t>(stream));
   if (e == cudaSuccess) e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
-  if (e != cudaSuccess) return cuda_fail(e, "reading counters");
+  if (e != cudaSuccess) return cuda_error(e, "reading counters");
   *dropped = c[kCntBad];
   return LMG_OK;
 }
@@ -441,11 +436,11 @@ int lmg_plan_info(lmg_plan* p, int64_t* out, void* stream) {
   int c[8];
   cudaError_t e = cudaMemcpyAsync(c, p->counters, sizeof(c), cudaMemcpyDeviceToHost, static_cast<cudaStream_t>(stream));
   if (e == cudaSuccess) e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
-  if (e != cudaSuccess) return cuda_fail(e, "reading counters");
+  if (e != cudaSuccess) return cuda_error(e, "reading counters");
   int total = 0;
   if (p->nvis >= 0) {
     e = cudaMemcpy(&total, p->offsets + (long long)p->n_strips * p->N, sizeof(int), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_fail(e, "reading offsets");
+    if (e != cudaSuccess) return cuda_error(e, "reading offsets");
   }
   out[0] = p->N;
   out[1] = p->n_image;

@@ -189,7 +189,7 @@ __global__ void k_bin_scatter(const VisPos* __restrict__ pos, const int2* __rest
 // records are placed from the front of the array and the others from the back, so that
 // the sweeps (which take items front to back, then back to front) start the heavy ones
 // first.
-constexpr int kMaxRowsPerBlock = 256;
+constexpr int kMaxRowsPerBlock = 512;
 
 __global__ void k_make_items(const int* __restrict__ offsets, int N, int n_strips, int rows_per_block,
                              int target, Item* __restrict__ items, int* __restrict__ counters, int cap) {

@@ -6,6 +6,9 @@
 #include <string>
 #include <vector>
 
+#include <cufft.h>
+
+#include "kernels.h"
 #include "lmg.h"
 
 namespace lmg {
@@ -42,5 +45,55 @@ int build_least_misfit(int W, double x0p, int Ms, lmg_table* t);
 // float32-rounded) table function; table.cpp.
 void correction_factors(const lmg_table* t, int64_t n_image, int64_t N, bool single_precision,
                         double* h_out);
+
+}  // namespace lmg
+
+// Plan state: binned positions of one uv set for one (table, grid size, pixel scale, dtype).
+struct lmg_plan {
+  int W = 0, Ms = 0, interp = 1, dtype = 0, Wp = 0;
+  int64_t n_image = 0, N = 0;
+  double x0 = 0, pixel_scale = 0, scale2 = 0;
+  int n_strips = 0, rows_per_block = 256, item_target = 1024, item_cap = 0, nchunks = 0;
+  int64_t max_vis = 0, nvis = -1;
+  int device = 0, sms = 0;
+  int blocks_grid = 0, blocks_degrid = 0;
+  bool tab_smem_grid = false, tab_smem_degrid = false;
+  int warps_grid = 8, warps_degrid = 8;
+  size_t smem_grid = 0, smem_degrid = 0;
+  int blocks_grid_comp = 0;
+  void* d_table = nullptr;
+  void* d_h = nullptr;
+  lmg::VisPos* pos = nullptr;
+  int* hist = nullptr;
+  int* offsets = nullptr;
+  int2* rank = nullptr;
+  int* partial = nullptr;
+  lmg::Rec* recs = nullptr;
+  lmg::Item* items = nullptr;
+  int* counters = nullptr;
+  void* spill = nullptr;
+  void* dpart = nullptr;
+  void* work = nullptr;      // N x N work grid (null in batch channels)
+  cufftHandle fft = 0;
+  bool fft_ok = false;
+};
+
+namespace lmg {
+
+// Options of plan creation used by the multi-channel batch: capacities sized for the
+// smallest bin parameters the tuner may choose, and no per-plan work grid or FFT plan.
+struct PlanOptions {
+  int min_rows_per_block = 256;
+  int min_item_target = 1024;
+  bool work_grid = true;
+  bool fft = true;
+};
+
+int plan_create(const lmg_table* t, int64_t n_image, double pixel_scale, int64_t max_vis, int dtype,
+                const PlanOptions& opt, lmg_plan** out);
+int plan_bin(lmg_plan* p, const double* uv, int64_t nvis, cudaStream_t st);
+void free_plan(lmg_plan* p);
+SweepArgs sweep_args(const lmg_plan* p);
+int cuda_error(cudaError_t e, const char* what);
 
 }  // namespace lmg

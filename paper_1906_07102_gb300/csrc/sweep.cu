@@ -1,339 +1,24 @@
-// Gridding and degridding sweeps (Eqs. 5-6 and their transpose, Section 4).
-//
-// The grid is cut into 32-column strips; a warp owns one work item (a range of rows of
-// one strip) and lane t owns column t of the strip. The item's records are sorted by
-// support-start row and visited in groups of kD = 2 rows, in chunks of up to 32 records
-// (the records and visibilities of the next two chunks are already in flight):
-//   1. lane l computes the 2W table weights of record l (Section 5.1 lookup) and stages
-//      them in shared memory: its first column, Cu_i w V (gridding) or Cu_i (degridding),
-//      and its Cv_j shifted by the record's row offset d in the group, so that entry q of
-//      the staged vector weights target row q of the group (q < T = W + kD - 1). The
-//      shifted vectors are stored entry-major, so when the lanes of a warp read entry q of
-//      different records they read one 128-byte row (one shared-memory wavefront);
-//   2. each lane builds the set of records whose support covers its column (32x32 bit
-//      transpose of the per-record cover masks) and visits them;
-//   3. gridding: lane t holds a ring of RS >= T accumulators (rows of its column) in
-//      registers and adds Cv'_q (Cu_i w V) to ring slot (base + q) -- a compile-time
-//      index, the group loop being unrolled over one ring period. After a group its kD rows
-//      are final and are stored as whole rows (256-byte coalesced stores for complex64).
-//      The W-1 rows past the item go to a spill buffer and are added by k_grid_spill once
-//      all items have stored their rows.
-//      degridding: the ring holds grid rows of the lane's column; lane t forms
-//      Cu_i sum_q Cv'_q G[row0 + q][t] for each covering record and stages it; lane l sums
-//      its record's W partial sums.
-// Every grid cell is written exactly once by the gridding sweep (no pre-zeroing, no
-// atomics except the spill rows).
-#include <cuda_runtime.h>
-
-#include <type_traits>
-
-#include "device_common.cuh"
-#include "kernels.h"
+// Single-plan gridding and degridding kernels: persistent CTAs whose warps take work items
+// from a counter and run the per-item sweeps of sweep_body.cuh; the spill and fix-up passes;
+// launch configuration.
+#include "sweep_body.cuh"
 
 namespace lmg {
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
-
-template <typename R> __host__ __device__ constexpr int wpad(int W) {
-  return sizeof(R) == 4 ? ((W + 3) & ~3) : ((W + 1) & ~1);
-}
-
-// Rows per group and the register ring: RS >= T = W + kD - 1 slots, a multiple of kD, so
-// that the group loop unrolled over P = RS / kD groups indexes every slot at compile time.
-constexpr int kD = 2;
-template <int W> struct Ring {
-  static constexpr int T = W + kD - 1;
-  static constexpr int R = kD * ((T + kD - 1) / kD);
-  static constexpr int P = R / kD;
-};
-
-template <int W, typename R> struct Stage {
-  // per warp: x0[32] | cvs[T][32] (entry-major) | cu[32][W] (degrid) | a or p [32][W] complex
-  static constexpr int T = Ring<W>::T;
-  static constexpr size_t x0_bytes = 32 * sizeof(int);
-  static constexpr size_t cv_bytes = 32 * T * sizeof(R);
-  static constexpr size_t cu_bytes = 32 * W * sizeof(R);
-  static constexpr size_t a_bytes = 32 * W * 2 * sizeof(R);
-  static constexpr size_t grid_bytes = x0_bytes + cv_bytes + a_bytes;
-  static constexpr size_t degrid_bytes = x0_bytes + cv_bytes + cu_bytes + a_bytes;
-};
-
-__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
-
-template <int T, int Tp, typename R>
-__device__ __forceinline__ void load_vec(const R* __restrict__ p, R (&v)[T]) {
-  if constexpr (sizeof(R) == 4 && Tp % 4 == 0) {
-    float tmp[Tp];
-#pragma unroll
-    for (int q = 0; q < Tp / 4; ++q) {
-      const float4 f = reinterpret_cast<const float4*>(p)[q];
-      tmp[4 * q] = f.x;
-      tmp[4 * q + 1] = f.y;
-      tmp[4 * q + 2] = f.z;
-      tmp[4 * q + 3] = f.w;
-    }
-#pragma unroll
-    for (int q = 0; q < T; ++q) v[q] = tmp[q];
-  } else if constexpr (sizeof(R) == 8 && Tp % 2 == 0) {
-    double tmp[Tp];
-#pragma unroll
-    for (int q = 0; q < Tp / 2; ++q) {
-      const double2 f = reinterpret_cast<const double2*>(p)[q];
-      tmp[2 * q] = f.x;
-      tmp[2 * q + 1] = f.y;
-    }
-#pragma unroll
-    for (int q = 0; q < T; ++q) v[q] = tmp[q];
-  } else {
-#pragma unroll
-    for (int q = 0; q < T; ++q) v[q] = p[q];
-  }
-}
-
-// Stages Cv shifted by d in [0, kD) rows, entry-major: out[q * 32] = cv[q - d] for
-// 0 <= q - d < W, else 0 (q < T).
-template <int W, typename R>
-__device__ __forceinline__ void stage_shifted(R* __restrict__ out, const R (&cv)[W], int d) {
-  constexpr int T = W + kD - 1;
-#pragma unroll
-  for (int q = 0; q < T; ++q) {
-    R v = R(0);
-#pragma unroll
-    for (int dd = 0; dd < kD; ++dd)
-      if (d == dd && q - dd >= 0 && q - dd < W) v = cv[q - dd];
-    out[q * 32] = v;
-  }
-}
-
-// Copy the table into shared memory (all threads of the CTA), or use it in place.
-template <typename R>
-__device__ __forceinline__ const R* stage_table(const SweepArgs& a, unsigned char* smem) {
-  const R* g = static_cast<const R*>(a.table);
-  if (!a.table_in_smem) return g;
-  R* s = reinterpret_cast<R*>(smem);
-  const int n = (a.Ms + 1) * a.Wp;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s[i] = g[i];
-  __syncthreads();
-  return s;
-}
-
-__device__ __forceinline__ int next_item(int* counter, int lane) {
-  int it = 0;
-  if (lane == 0) it = atomicAdd(counter, 1);
-  return __shfl_sync(0xffffffffu, it, 0);
-}
-
-// Work index -> item: heavy items were placed from the front of the array, light ones
-// from the back.
-__device__ __forceinline__ int work_total(const int* counters, int cap, int& nfront) {
-  nfront = min(counters[kCntItems], cap);
-  return min(nfront + counters[kCntItemsBack], cap);
-}
-__device__ __forceinline__ int item_slot(int w, int nfront, int cap) { return w < nfront ? w : cap - 1 - (w - nfront); }
-
-// Calls f(std::integral_constant<int, p>) for the runtime phase p in [0, P).
-template <int P, int I = 0, typename F>
-__device__ __forceinline__ void dispatch(int p, F&& f) {
-  if constexpr (I < P) {
-    if (p == I) f(std::integral_constant<int, I>{});
-    else dispatch<P, I + 1>(p, f);
-  }
-}
-
-// Record prefetch for the software pipeline: one record and its visibility (and weight)
-// per lane for a chunk starting at `start`.
-template <typename R> struct Fetch {
-  Rec rc;
-  typename Cplx<R>::T v;
-  R wt;
-};
-
-// Error-free addition s + e = a + b (Knuth TwoSum); a receives s, lo accumulates e.
-__device__ __forceinline__ void two_sum_acc(float& a, float& lo, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bp = __fsub_rn(s, a);
-  const float ap = __fsub_rn(s, bp);
-  lo += __fsub_rn(a, ap) + __fsub_rn(b, bp);
-  a = s;
-}
-
-// Resident CTAs per SM the register allocation must allow.
-template <int W, typename R, bool COMP = false> constexpr int min_blocks() {
-  return COMP ? 2 : ((sizeof(R) == 4 && W <= 8) ? 3 : 1);
-}
-
 template <int W, typename R, bool COMP>
 __global__ void __launch_bounds__(kThreads, min_blocks<W, R, COMP>()) k_grid_sweep(const SweepArgs a) {
-  using C2 = typename Cplx<R>::T;
-  using St = Stage<W, R>;
-  constexpr int Wp = wpad<R>(W);
-  constexpr int RS = Ring<W>::R, P = Ring<W>::P, TT = Ring<W>::T;
-  constexpr bool kPk = sizeof(R) == 4 && !COMP;
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const R* tab = stage_table<R>(a, smem);
+  const R* tab = stage_table<R>(a.table, (a.Ms + 1) * a.Wp, a.table_in_smem != 0, smem);
   const size_t tab_bytes = a.table_in_smem ? align16(size_t(a.Ms + 1) * a.Wp * sizeof(R)) : 0;
-  unsigned char* my = smem + tab_bytes + warp * align16(St::grid_bytes);
-  int* s_x0 = reinterpret_cast<int*>(my);
-  R* s_cv = reinterpret_cast<R*>(my + St::x0_bytes);
-  C2* s_a = reinterpret_cast<C2*>(my + St::x0_bytes + St::cv_bytes);
-
-  const Rec* __restrict__ recs = a.recs;
-  const C2* __restrict__ vis = static_cast<const C2*>(a.vis);
-  const R* __restrict__ wts = static_cast<const R*>(a.weights);
-  C2* __restrict__ grid = static_cast<C2*>(a.grid);
-  C2* __restrict__ spill = static_cast<C2*>(a.spill);
-  const int N = a.N;
+  unsigned char* my = smem + tab_bytes + warp * align16(Stage<W, R>::grid_bytes);
   int nfront;
   const int total = work_total(a.counters, a.item_cap, nfront);
-
-  auto fetch_rec = [&](int start, int end, Fetch<R>& f) {
-    if (start + lane < end) f.rc = recs[start + lane];
-  };
-  auto fetch_vis = [&](int start, int end, Fetch<R>& f) {
-    if (start + lane < end) {
-      f.v = vis[f.rc.idx];
-      f.wt = wts != nullptr ? wts[f.rc.idx] : R(1);
-    }
-  };
-
-  for (int w = next_item(a.counters + kCntGridWork, lane); w < total; w = next_item(a.counters + kCntGridWork, lane)) {
-    const int slot = item_slot(w, nfront, a.item_cap);
-    const Item item = a.items[slot];
-    const int* __restrict__ off = a.offsets + static_cast<long long>(item.strip) * N;
-    const int col = item.strip * kStrip + lane;
-    const int nrows = item.r1 - item.r0;
-    // ring slot x % RS accumulates relative row x of column `col` (packed (re, im) pairs on
-    // the plain float32 path, separate real arrays otherwise)
-    R acc_re[RS], acc_im[RS], lo_re[RS], lo_im[RS];
-    unsigned long long acc2[RS];
-#pragma unroll
-    for (int q = 0; q < RS; ++q) {
-      acc_re[q] = acc_im[q] = lo_re[q] = lo_im[q] = R(0);
-      acc2[q] = 0ull;
-    }
-    // software pipeline over 32-record windows of the item (window k = records
-    // rb + 32k .. rb + 32k + 31, lane l holding record rb + 32k + l): while window k is
-    // processed, the visibilities of window k+1 and the records of window k+2 are in flight
-    const int rb = off[item.r0], rend = off[item.r1];
-    int wbase = rb, cstart = rb;
-    Fetch<R> f0, f1, f2;
-    fetch_rec(rb, rend, f0);
-    fetch_rec(rb + 32, rend, f1);
-    fetch_vis(rb, rend, f0);
-    fetch_vis(rb + 32, rend, f1);
-    fetch_rec(rb + 64, rend, f2);
-    for (int g0 = 0; g0 < nrows; g0 += RS) {
-#pragma unroll
-      for (int gp = 0; gp < P; ++gp) {
-        const int gb = g0 + gp * kD;
-        if (gb < nrows) {
-          const int row0 = item.r0 + gb;
-          const int re = off[min(row0 + kD, item.r1)];
-          while (cstart < re) {
-            // chunk: records [cstart, ce) of window wbase, staged by lanes cstart - wbase ..
-            const int ce = min(re, wbase + 32);
-            unsigned cover = 0u;
-            if (lane >= cstart - wbase && lane < ce - wbase) {
-              const int xrel = rec_xrel(f0.rc.rx);
-              R cu[W], cv[W];
-              table_weights<W, R>(tab, Wp, a.Ms, a.interp, f0.rc.su, cu);
-              table_weights<W, R>(tab, Wp, a.Ms, a.interp, f0.rc.sv, cv);
-              C2 v = f0.v;
-              v.x *= f0.wt;
-              v.y *= f0.wt;
-              s_x0[lane] = xrel;
-              stage_shifted<W, R>(s_cv + lane, cv, rec_row(f0.rc.rx) - row0);
-#pragma unroll
-              for (int i = 0; i < W; ++i) {
-                C2 t;
-                t.x = cu[i] * v.x;
-                t.y = cu[i] * v.y;
-                s_a[lane * W + i] = t;
-              }
-              cover = cover_mask(xrel, W);
-            }
-            __syncwarp();
-            unsigned M = transpose32(cover, lane);
-            while (M) {
-              const int l = __ffs(M) - 1;
-              M &= M - 1u;
-              const C2 ai = s_a[l * W + (lane - s_x0[l])];
-#pragma unroll
-              for (int q = 0; q < TT; ++q) {
-                const R c = s_cv[q * 32 + l];
-                const int k = (gp * kD + q) % RS;
-                if constexpr (kPk) {
-                  acc2[k] = f2fma(f2pack(c, c), f2pack(ai.x, ai.y), acc2[k]);
-                } else if constexpr (COMP) {
-                  two_sum_acc(acc_re[k], lo_re[k], c * ai.x);
-                  two_sum_acc(acc_im[k], lo_im[k], c * ai.y);
-                } else {
-                  acc_re[k] = fma(c, ai.x, acc_re[k]);
-                  acc_im[k] = fma(c, ai.y, acc_im[k]);
-                }
-              }
-            }
-            __syncwarp();
-            cstart = ce;
-            if (cstart == wbase + 32) {
-              wbase += 32;
-              f0 = f1;
-              f1 = f2;
-              fetch_vis(wbase + 32, rend, f1);
-              fetch_rec(wbase + 64, rend, f2);
-            }
-          }
-          // rows row0 .. row0 + kD - 1 are complete: store them and recycle their slots
-#pragma unroll
-          for (int d = 0; d < kD; ++d) {
-            const int k = (gp * kD + d) % RS;
-            if (gb + d < nrows) {
-              C2 o;
-              if constexpr (kPk) {
-                const float2 f = f2unpack(acc2[k]);
-                o.x = f.x;
-                o.y = f.y;
-              } else if constexpr (COMP) {
-                o.x = acc_re[k] + lo_re[k];
-                o.y = acc_im[k] + lo_im[k];
-              } else {
-                o.x = acc_re[k];
-                o.y = acc_im[k];
-              }
-              grid[static_cast<size_t>(row0 + d) * N + col] = o;
-              acc_re[k] = acc_im[k] = lo_re[k] = lo_im[k] = R(0);
-              acc2[k] = 0ull;
-            }
-          }
-        }
-      }
-    }
-    // spill: slot q holds relative row nrows + ((q - nrows) mod RS); the W - 1 rows after
-    // the item carry partial sums
-    C2* sp = spill + static_cast<size_t>(slot) * RS * kStrip;
-#pragma unroll
-    for (int q = 0; q < RS; ++q) {
-      C2 o;
-      if constexpr (kPk) {
-        const float2 f = f2unpack(acc2[q]);
-        o.x = f.x;
-        o.y = f.y;
-      } else if constexpr (COMP) {
-        o.x = acc_re[q] + lo_re[q];
-        o.y = acc_im[q] + lo_im[q];
-      } else {
-        o.x = acc_re[q];
-        o.y = acc_im[q];
-      }
-      sp[q * kStrip + lane] = o;
-    }
-  }
+  for (int w = next_item(a.counters + kCntGridWork, lane); w < total; w = next_item(a.counters + kCntGridWork, lane))
+    grid_item<W, R, COMP>(a, tab, my, item_slot(w, nfront, a.item_cap), lane);
 }
 
-// Adds each item's spill rows into the grid (after every item stored its own rows).
 template <typename R>
 __global__ void k_grid_spill(const Item* __restrict__ items, const int* __restrict__ counters, int item_cap,
                              int W, int RS, int N, const typename Cplx<R>::T* __restrict__ spill,
@@ -343,181 +28,32 @@ __global__ void k_grid_spill(const Item* __restrict__ items, const int* __restri
   const long long gw = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const long long n = static_cast<long long>(total) * RS;
-  for (long long w = gw; w < n; w += (static_cast<long long>(gridDim.x) * blockDim.x) >> 5) {
-    const int slot = item_slot(static_cast<int>(w / RS), nfront, item_cap);
-    const int q = static_cast<int>(w % RS);
-    const Item item = items[slot];
-    const int nrows = item.r1 - item.r0;
-    if (nrows <= 0 || item.nrec == 0) continue;
-    const int j = ((q - nrows) % RS + RS) % RS;
-    if (j > W - 2) continue;
-    const int row = (item.r1 + j) % N;
-    const auto v = spill[(static_cast<size_t>(slot) * RS + q) * kStrip + lane];
-    red_add(grid + static_cast<size_t>(row) * N + item.strip * kStrip + lane, v);
-  }
+  for (long long w = gw; w < n; w += (static_cast<long long>(gridDim.x) * blockDim.x) >> 5)
+    spill_unit<R>(items, nfront, item_cap, W, RS, N, spill, grid, w, lane);
 }
 
 template <int W, typename R>
 __global__ void __launch_bounds__(kThreads, min_blocks<W, R>()) k_degrid_sweep(const SweepArgs a) {
-  using C2 = typename Cplx<R>::T;
-  using St = Stage<W, R>;
-  constexpr int Wp = wpad<R>(W);
-  constexpr int RS = Ring<W>::R, P = Ring<W>::P, TT = Ring<W>::T;
-  constexpr bool kPk = sizeof(R) == 4;
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const R* tab = stage_table<R>(a, smem);
+  const R* tab = stage_table<R>(a.table, (a.Ms + 1) * a.Wp, a.table_in_smem != 0, smem);
   const size_t tab_bytes = a.table_in_smem ? align16(size_t(a.Ms + 1) * a.Wp * sizeof(R)) : 0;
-  unsigned char* my = smem + tab_bytes + warp * align16(St::degrid_bytes);
-  int* s_x0 = reinterpret_cast<int*>(my);
-  R* s_cv = reinterpret_cast<R*>(my + St::x0_bytes);
-  R* s_cu = reinterpret_cast<R*>(my + St::x0_bytes + St::cv_bytes);
-  C2* s_p = reinterpret_cast<C2*>(my + St::x0_bytes + St::cv_bytes + St::cu_bytes);
-
-  const Rec* __restrict__ recs = a.recs;
-  const C2* __restrict__ G = static_cast<const C2*>(a.grid_in);
-  C2* __restrict__ out = static_cast<C2*>(a.vis_out);
-  C2* __restrict__ dpart = static_cast<C2*>(a.dpart);
-  const int N = a.N;
+  unsigned char* my = smem + tab_bytes + warp * align16(Stage<W, R>::degrid_bytes);
   int nfront;
   const int total = work_total(a.counters, a.item_cap, nfront);
-
   for (int w = next_item(a.counters + kCntDegridWork, lane); w < total;
        w = next_item(a.counters + kCntDegridWork, lane)) {
     const Item item = a.items[item_slot(w, nfront, a.item_cap)];
-    if (item.nrec == 0) continue;
-    const int* __restrict__ off = a.offsets + static_cast<long long>(item.strip) * N;
-    const int col = item.strip * kStrip + lane;
-    const int nrows = item.r1 - item.r0;
-    // ring slot x % RS holds grid row item.r0 + x of column `col`; rows 0 .. TT - kD - 1
-    // are loaded up front, each group loads the kD rows that complete its window
-    R g_re[RS], g_im[RS];
-    unsigned long long g2[RS];
-#pragma unroll
-    for (int x = 0; x < TT - kD; ++x) {
-      const C2 v = G[static_cast<size_t>((item.r0 + x) % N) * N + col];
-      g_re[x] = v.x;
-      g_im[x] = v.y;
-      if constexpr (kPk) g2[x] = f2pack(float(v.x), float(v.y));
-    }
-    const int rb = off[item.r0], rend = off[item.r1];
-    int wbase = rb, cstart = rb;
-    Rec rc0{0u, 0, 0u, 0u}, rc1{0u, 0, 0u, 0u}, rc2{0u, 0, 0u, 0u};
-    if (rb + lane < rend) rc0 = recs[rb + lane];
-    if (rb + 32 + lane < rend) rc1 = recs[rb + 32 + lane];
-    if (rb + 64 + lane < rend) rc2 = recs[rb + 64 + lane];
-    for (int g0 = 0; g0 < nrows; g0 += RS) {
-#pragma unroll
-      for (int gp = 0; gp < P; ++gp) {
-        const int gb = g0 + gp * kD;
-        if (gb < nrows) {
-          const int row0 = item.r0 + gb;
-#pragma unroll
-          for (int d = 0; d < kD; ++d) {
-            const int x = gb + TT - kD + d;
-            const C2 v = G[static_cast<size_t>((item.r0 + x) % N) * N + col];
-            g_re[(gp * kD + TT - kD + d) % RS] = v.x;
-            g_im[(gp * kD + TT - kD + d) % RS] = v.y;
-            if constexpr (kPk) g2[(gp * kD + TT - kD + d) % RS] = f2pack(float(v.x), float(v.y));
-          }
-          const int re = off[min(row0 + kD, item.r1)];
-          while (cstart < re) {
-            const int ce = min(re, wbase + 32);
-            const bool mine = lane >= cstart - wbase && lane < ce - wbase;
-            const int xrel = rec_xrel(rc0.rx);
-            unsigned cover = 0u;
-            if (mine) {
-              R cu[W], cv[W];
-              table_weights<W, R>(tab, Wp, a.Ms, a.interp, rc0.su, cu);
-              table_weights<W, R>(tab, Wp, a.Ms, a.interp, rc0.sv, cv);
-              s_x0[lane] = xrel;
-              stage_shifted<W, R>(s_cv + lane, cv, rec_row(rc0.rx) - row0);
-#pragma unroll
-              for (int j = 0; j < W; ++j) s_cu[lane * W + j] = cu[j];
-              cover = cover_mask(xrel, W);
-            }
-            __syncwarp();
-            unsigned M = transpose32(cover, lane);
-            while (M) {
-              const int l = __ffs(M) - 1;
-              M &= M - 1u;
-              const int i = lane - s_x0[l];
-              R sr = R(0), si = R(0);
-              if constexpr (kPk) {
-                unsigned long long s2 = 0ull;
-#pragma unroll
-                for (int q = 0; q < TT; ++q) {
-                  const R c = s_cv[q * 32 + l];
-                  s2 = f2fma(f2pack(c, c), g2[(gp * kD + q) % RS], s2);
-                }
-                const float2 f = f2unpack(s2);
-                sr = f.x;
-                si = f.y;
-              } else {
-#pragma unroll
-                for (int q = 0; q < TT; ++q) {
-                  const R c = s_cv[q * 32 + l];
-                  sr = fma(c, g_re[(gp * kD + q) % RS], sr);
-                  si = fma(c, g_im[(gp * kD + q) % RS], si);
-                }
-              }
-              const R cu_i = s_cu[l * W + i];
-              C2 p;
-              p.x = cu_i * sr;
-              p.y = cu_i * si;
-              s_p[l * W + i] = p;
-            }
-            __syncwarp();
-            if (mine) {
-              const int i0 = max(0, -xrel), i1 = min(W, kStrip - xrel);
-              R vr = R(0), vi = R(0);
-              for (int ii = i0; ii < i1; ++ii) {
-                const C2 p = s_p[lane * W + ii];
-                vr += p.x;
-                vi += p.y;
-              }
-              C2 o;
-              o.x = vr;
-              o.y = vi;
-              if (xrel >= 0) out[rc0.idx] = o;
-              else dpart[rc0.idx] = o;
-            }
-            __syncwarp();
-            cstart = ce;
-            if (cstart == wbase + 32) {
-              wbase += 32;
-              rc0 = rc1;
-              rc1 = rc2;
-              if (wbase + 64 + lane < rend) rc2 = recs[wbase + 64 + lane];
-            }
-          }
-        }
-      }
-    }
+    degrid_item<W, R>(a, tab, my, item, lane);
   }
 }
 
-// Adds the partial sums of secondary records (supports crossing a strip boundary) and
-// zeroes the outputs of dropped positions; one pass over the visibilities' positions.
 template <typename R>
 __global__ void k_degrid_fixup(const VisPos* __restrict__ pos, long long nvis, int W,
                                const typename Cplx<R>::T* __restrict__ dpart, typename Cplx<R>::T* __restrict__ out) {
   const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
-  for (long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; k < nvis; k += stride) {
-    const int x0 = pos[k].x0;
-    if (x0 < 0) {
-      typename Cplx<R>::T z;
-      z.x = 0;
-      z.y = 0;
-      out[k] = z;
-    } else if ((x0 % kStrip) + W > kStrip) {
-      auto v = out[k];
-      const auto p = dpart[k];
-      v.x += p.x;
-      v.y += p.y;
-      out[k] = v;
-    }
-  }
+  for (long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; k < nvis; k += stride)
+    fixup_one<R>(pos, k, W, dpart, out);
 }
 
 template <int W, typename R, bool COMP> void* grid_kernel_ptr() {
@@ -553,13 +89,6 @@ void* kernel_for(int W, int dtype, int accum, bool degrid) {
     case 16: return pick_kernel<16>(dtype, accum, degrid);
     default: return nullptr;
   }
-}
-
-size_t stage_bytes(int W, int dtype, bool degrid) {
-  const size_t rs = dtype ? 8 : 4;
-  const int T = W + kD - 1;
-  const size_t x0 = 32 * sizeof(int), cv = 32 * size_t(T) * rs, cu = 32 * size_t(W) * rs, ab = 32 * W * 2 * rs;
-  return align16(x0 + cv + (degrid ? cu : 0) + ab);
 }
 
 }  // namespace

@@ -43,6 +43,15 @@ _SIGS = {
     "lmg_dirty_image": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, _vp]),
     "lmg_predict_vis": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "lmg_grid_static": (ctypes.c_int, [_vp, _i64, ctypes.c_double, _vp, _i64, _vp, _vp, _vp, _vp]),
+    "lmg_batch_create": (ctypes.c_int, [ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.POINTER(_vp)]),
+    "lmg_batch_free": (ctypes.c_int, [_vp]),
+    "lmg_batch_bin": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "lmg_batch_grid": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "lmg_batch_degrid": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "lmg_batch_dirty_image": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "lmg_batch_predict_vis": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "lmg_batch_tune": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "lmg_batch_info": (ctypes.c_int, [_vp, _vp]),
     "lmg_last_error": (ctypes.c_char_p, []),
     "lmg_version": (ctypes.c_char_p, []),
 }
@@ -264,6 +273,130 @@ def grid_static(table, n_image, pixel_scale, uv, vis, weights=None, out=None):
     _check(lib().lmg_grid_static(table._h, n_image, pixel_scale, _ptr(uv), nvis, _ptr(vis), _ptr(weights),
                                  _ptr(out), _stream()))
     return out
+
+
+def _ptr_array(tensors):
+    """Host array of device pointers (NULL for None entries)."""
+    arr = (_vp * len(tensors))()
+    for i, x in enumerate(tensors):
+        arr[i] = x.data_ptr() if x is not None else None
+    return arr
+
+
+class Batch:
+    """Many independent channels (own table, grid size, pixel scale and uv set each),
+    gridded and degridded together: one persistent sweep launch per support width, one
+    batched FFT per grid size, each operation captured into a CUDA graph (complex64)."""
+
+    def __init__(self, tables, n_images, pixel_scales, max_vis):
+        n = len(tables)
+        if not (len(n_images) == len(pixel_scales) == len(max_vis) == n):
+            raise ValueError("per-channel argument lists must have equal lengths")
+        self.tables = list(tables)
+        self.n_images = [int(v) for v in n_images]
+        self.N = [int(round(ni / t.x0)) for ni, t in zip(self.n_images, self.tables)]
+        tabs = (_vp * n)(*[t._h for t in self.tables])
+        nim = np.asarray(self.n_images, dtype=np.int64)
+        ps = np.asarray(pixel_scales, dtype=np.float64)
+        mv = np.asarray(max_vis, dtype=np.int64)
+        h = _vp()
+        _check(lib().lmg_batch_create(n, ctypes.cast(tabs, _vp), nim.ctypes.data_as(_vp), ps.ctypes.data_as(_vp),
+                                      mv.ctypes.data_as(_vp), ctypes.byref(h)))
+        self._h = h
+        self.n_chan = n
+        self.nvis = None
+
+    def bin(self, uvs):
+        """Bins uvs[c] (CUDA float64 [nvis_c, 2], wavelengths); the tensors must stay alive
+        while the batch uses them (the tuner re-bins from them)."""
+        import torch
+        if len(uvs) != self.n_chan:
+            raise ValueError("one uv tensor per channel")
+        for u in uvs:
+            _need(u, torch.float64, None, "uv")
+        self._uvs = list(uvs)
+        nv = np.asarray([u.shape[0] for u in uvs], dtype=np.int64)
+        _check(lib().lmg_batch_bin(self._h, ctypes.cast(_ptr_array(uvs), _vp), nv.ctypes.data_as(_vp), _stream()))
+        self.nvis = [int(v) for v in nv]
+        return self
+
+    def _vis_lists(self, vis, weights):
+        import torch
+        for c, v in enumerate(vis):
+            _need(v, torch.complex64, (self.nvis[c],), "vis")
+        if weights is not None:
+            for c, w in enumerate(weights):
+                if w is not None:
+                    _need(w, torch.float32, (self.nvis[c],), "weights")
+        return _ptr_array(vis), (_ptr_array(weights) if weights is not None else None)
+
+    def grid(self, vis, weights=None, out=None):
+        import torch
+        if out is None:
+            out = [torch.empty((N, N), dtype=torch.complex64, device=v.device) for N, v in zip(self.N, vis)]
+        for c, g in enumerate(out):
+            _need(g, torch.complex64, (self.N[c], self.N[c]), "grid")
+        va, wa = self._vis_lists(vis, weights)
+        _check(lib().lmg_batch_grid(self._h, ctypes.cast(va, _vp), ctypes.cast(wa, _vp) if wa is not None else None,
+                                    ctypes.cast(_ptr_array(out), _vp), _stream()))
+        return out
+
+    def degrid(self, grids, out=None):
+        import torch
+        for c, g in enumerate(grids):
+            _need(g, torch.complex64, (self.N[c], self.N[c]), "grid")
+        if out is None:
+            out = [torch.empty(n, dtype=torch.complex64, device=g.device) for n, g in zip(self.nvis, grids)]
+        for c, v in enumerate(out):
+            _need(v, torch.complex64, (self.nvis[c],), "vis_out")
+        _check(lib().lmg_batch_degrid(self._h, ctypes.cast(_ptr_array(grids), _vp), ctypes.cast(_ptr_array(out), _vp),
+                                      _stream()))
+        return out
+
+    def dirty_image(self, vis, weights=None, out=None):
+        import torch
+        if out is None:
+            out = [torch.empty((n, n), dtype=torch.complex64, device=v.device) for n, v in zip(self.n_images, vis)]
+        for c, g in enumerate(out):
+            _need(g, torch.complex64, (self.n_images[c], self.n_images[c]), "image")
+        va, wa = self._vis_lists(vis, weights)
+        _check(lib().lmg_batch_dirty_image(self._h, ctypes.cast(va, _vp),
+                                           ctypes.cast(wa, _vp) if wa is not None else None,
+                                           ctypes.cast(_ptr_array(out), _vp), _stream()))
+        return out
+
+    def predict_vis(self, images, out=None):
+        import torch
+        for c, g in enumerate(images):
+            _need(g, torch.complex64, (self.n_images[c], self.n_images[c]), "image")
+        if out is None:
+            out = [torch.empty(n, dtype=torch.complex64, device=g.device) for n, g in zip(self.nvis, images)]
+        for c, v in enumerate(out):
+            _need(v, torch.complex64, (self.nvis[c],), "vis_out")
+        _check(lib().lmg_batch_predict_vis(self._h, ctypes.cast(_ptr_array(images), _vp),
+                                           ctypes.cast(_ptr_array(out), _vp), _stream()))
+        return out
+
+    def tune(self, vis):
+        """Autotuner: returns the chosen (rows per bin, records per item, warps per CTA,
+        tables in shared memory) after re-binning with it."""
+        va, _ = self._vis_lists(vis, None)
+        chosen = (ctypes.c_int * 4)()
+        _check(lib().lmg_batch_tune(self._h, ctypes.cast(va, _vp), _stream(), ctypes.cast(chosen, _vp)))
+        return tuple(chosen)
+
+    def info(self):
+        out = np.zeros(8, dtype=np.int64)
+        _check(lib().lmg_batch_info(self._h, out.ctypes.data_as(_vp)))
+        keys = ("channels", "w_classes", "size_classes", "nvis", "rows_per_bin", "records_per_item", "warps",
+                "graphs_captured")
+        return dict(zip(keys, (int(v) for v in out)))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.lmg_batch_free(h)
+            self._h = None
 
 
 def _autograd():

@@ -142,3 +142,21 @@ def test_plan_argument_errors_precede_device_work(lmg):
                                            (40, 1e-3, 10, 0, "multiple of 32")):
         assert L.lmg_plan_create(t._h, n_img, scale, maxv, dtype, ctypes.byref(h)) == -1
         assert msg in L.lmg_last_error().decode()
+
+
+def test_batch_argument_errors_precede_device_work(lmg):
+    L = lmg.lib()
+    h = ctypes.c_void_p()
+    assert L.lmg_batch_create(0, None, None, None, None, ctypes.byref(h)) == -1
+    assert "n_chan" in L.lmg_last_error().decode()
+    assert L.lmg_batch_create(2, None, None, None, None, ctypes.byref(h)) == -1
+    tabs = (ctypes.c_void_p * 2)(None, None)
+    n = np.array([64, 64], dtype=np.int64)
+    s = np.array([1e-3, 1e-3])
+    assert L.lmg_batch_create(2, ctypes.cast(tabs, ctypes.c_void_p), n.ctypes.data_as(ctypes.c_void_p),
+                              s.ctypes.data_as(ctypes.c_void_p), n.ctypes.data_as(ctypes.c_void_p),
+                              ctypes.byref(h)) == -1
+    assert "tables[0]" in L.lmg_last_error().decode()
+    assert L.lmg_batch_bin(None, None, None, None) == -1
+    assert L.lmg_batch_grid(None, None, None, None, None) == -1
+    assert L.lmg_batch_info(None, None) == -1
