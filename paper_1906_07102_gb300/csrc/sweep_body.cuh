@@ -6,12 +6,14 @@
 // one strip) and lane t owns column t of the strip. The item's records are sorted by
 // support-start row and visited in groups of kD = 2 rows, in chunks of up to 32 records
 // (the records and visibilities of the next two chunks are already in flight):
-//   1. lane l computes the 2W table weights of record l (Section 5.1 lookup) and stages
-//      them in shared memory: its first column, Cu_i w V (gridding) or Cu_i (degridding),
-//      and its Cv_j shifted by the record's row offset d in the group, so that entry q of
-//      the staged vector weights target row q of the group (q < T = W + kD - 1). The
-//      shifted vectors are stored entry-major, so when the lanes of a warp read entry q of
-//      different records they read one 128-byte row (one shared-memory wavefront);
+//   1. the chunk's 2W table weights per record (Section 5.1 lookup) are staged in shared
+//      memory: Cu_i w V (gridding) or Cu_i (degridding), and Cv_j shifted by the record's
+//      row offset d in the group, so that entry q of the staged vector weights target row
+//      q of the group (q < T = W + kD - 1). G lanes share a record and look up one entry
+//      each (a lane per record would read 32 random table rows per instruction, which
+//      serialises on shared-memory banks). The shifted vectors are stored entry-major
+//      with a row pitch of 32 + 32/G, so that lanes reading entry q of different records
+//      hit distinct banks and so do the G lanes storing one record's entries;
 //   2. each lane builds the set of records whose support covers its column (32x32 bit
 //      transpose of the per-record cover masks) and visits them;
 //   3. gridding: lane t holds a ring of RS >= T accumulators (rows of its column) in
@@ -52,31 +54,84 @@ template <int W> struct Ring {
   static constexpr int P = R / kD;
 };
 
+// Cooperative table lookup while staging a chunk: G lanes share one record (each computes
+// one table entry), P = 32 / G records per round.
+template <int W> struct Coop {
+  static constexpr int G = W <= 4 ? 4 : (W <= 8 ? 8 : 16);
+  static constexpr int P = 32 / G;
+  // Row pitch (elements) of the staged Cv: entry q of record l sits at q * pitch + l. The
+  // extra P elements put the entries of the P records of one staging round in distinct
+  // banks, while the sweep's reads (entry q of different records) stay conflict-free.
+  static constexpr int pitch = 32 + P;
+};
+__host__ __device__ constexpr int coop_group(int W) { return W <= 4 ? 4 : (W <= 8 ? 8 : 16); }
+
+__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
 template <int W, typename R> struct Stage {
-  // per warp: x0[32] | cvs[T][32] (entry-major) | cu[32][W] (degrid) | a or p [32][W] complex
+  // per warp: x0[32] | cvs[T][pitch] (entry-major) | cu[32][W] (degrid) | a or p [32][W] complex
   static constexpr int T = Ring<W>::T;
   static constexpr size_t x0_bytes = 32 * sizeof(int);
-  static constexpr size_t cv_bytes = 32 * T * sizeof(R);
+  static constexpr size_t cv_bytes = align16(size_t(T) * Coop<W>::pitch * sizeof(R));
   static constexpr size_t cu_bytes = 32 * W * sizeof(R);
   static constexpr size_t a_bytes = 32 * W * 2 * sizeof(R);
   static constexpr size_t grid_bytes = x0_bytes + cv_bytes + a_bytes;
   static constexpr size_t degrid_bytes = x0_bytes + cv_bytes + cu_bytes + a_bytes;
 };
 
-__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+// Interpolated table entry i at coordinate S (the arithmetic of table_weights, one entry).
+template <typename R>
+__device__ __forceinline__ R table_entry(const R* __restrict__ tab, int Wp, int Ms, int interp, unsigned S, int i) {
+  const unsigned long long Pm = static_cast<unsigned long long>(S) * static_cast<unsigned>(Ms);
+  if (interp) {
+    const int k = static_cast<int>(Pm >> 32);
+    const R f = static_cast<R>(static_cast<unsigned>(Pm & 0xffffffffull)) * static_cast<R>(2.3283064365386962890625e-10);
+    const R* r0 = tab + static_cast<size_t>(k) * Wp;
+    const R a0 = r0[i];
+    return a0 + f * (r0[Wp + i] - a0);
+  }
+  const int k = static_cast<int>((Pm + 0x80000000ull) >> 32);
+  return tab[static_cast<size_t>(k) * Wp + i];
+}
 
-// Stages Cv shifted by d in [0, kD) rows, entry-major: out[q * 32] = cv[q - d] for
-// 0 <= q - d < W, else 0 (q < T).
-template <int W, typename R>
-__device__ __forceinline__ void stage_shifted(R* __restrict__ out, const R (&cv)[W], int d) {
-  constexpr int T = W + kD - 1;
-#pragma unroll
-  for (int q = 0; q < T; ++q) {
-    R v = R(0);
-#pragma unroll
-    for (int dd = 0; dd < kD; ++dd)
-      if (d == dd && q - dd >= 0 && q - dd < W) v = cv[q - dd];
-    out[q * 32] = v;
+// Stages the weights of a chunk's records, held one per lane by lanes lo .. hi-1 (su, sv,
+// row offset d in the group, and for gridding w V): Cv shifted by d into s_cv (entry q of
+// record l at q * pitch + l, zero for q outside [d, d + W)) and Cu, times w V when
+// gridding, into s_u[l * W + i]. G lanes share a record and compute one table entry each,
+// so a round's table reads touch P rows instead of 32 rows per instruction.
+template <int W, typename R, bool GRID>
+__device__ __forceinline__ void stage_chunk(const R* __restrict__ tab, int Wp, int Ms, int interp, int lo, int hi,
+                                            unsigned su, unsigned sv, int d, R wx, R wy, R* __restrict__ s_cv,
+                                            void* __restrict__ s_u, int lane) {
+  using C2 = typename Cplx<R>::T;
+  constexpr int G = Coop<W>::G, P = Coop<W>::P, pitch = Coop<W>::pitch, TT = Ring<W>::T;
+  const int g = lane / G, i = lane % G;
+  for (int r0 = lo; r0 < hi; r0 += P) {
+    const int r = r0 + g, src = r & 31;
+    const unsigned su_r = __shfl_sync(0xffffffffu, su, src);
+    const unsigned sv_r = __shfl_sync(0xffffffffu, sv, src);
+    const int d_r = __shfl_sync(0xffffffffu, d, src);
+    R wx_r = R(0), wy_r = R(0);
+    if constexpr (GRID) {
+      wx_r = __shfl_sync(0xffffffffu, wx, src);
+      wy_r = __shfl_sync(0xffffffffu, wy, src);
+    }
+    if (r < hi) {
+      if (i < W) {
+        const R cu = table_entry<R>(tab, Wp, Ms, interp, su_r, i);
+        const R cv = table_entry<R>(tab, Wp, Ms, interp, sv_r, i);
+        if constexpr (GRID) {
+          C2 t;
+          t.x = cu * wx_r;
+          t.y = cu * wy_r;
+          static_cast<C2*>(s_u)[r * W + i] = t;
+        } else {
+          static_cast<R*>(s_u)[r * W + i] = cu;
+        }
+        s_cv[(i + d_r) * pitch + r] = cv;
+      }
+      for (int z = i; z < TT - W; z += G) s_cv[(z < d_r ? z : z + W) * pitch + r] = R(0);
+    }
   }
 }
 
@@ -177,7 +232,7 @@ __device__ __forceinline__ void grid_item(const SweepArgs& a, const R* __restric
   // processed, the visibilities of window k+1 and the records of window k+2 are in flight
   const int rb = off[item.r0], rend = off[item.r1];
   int wbase = rb, cstart = rb;
-  Fetch<R> f0, f1, f2;
+  Fetch<R> f0{}, f1{}, f2{};
   fetch_rec(rb, rend, f0);
   fetch_rec(rb + 32, rend, f1);
   fetch_vis(rb, rend, f0);
@@ -193,26 +248,13 @@ __device__ __forceinline__ void grid_item(const SweepArgs& a, const R* __restric
         while (cstart < re) {
           // chunk: records [cstart, ce) of window wbase, staged by lanes cstart - wbase ..
           const int ce = min(re, wbase + 32);
-          unsigned cover = 0u;
-          if (lane >= cstart - wbase && lane < ce - wbase) {
-            const int xrel = rec_xrel(f0.rc.rx);
-            R cu[W], cv[W];
-            table_weights<W, R>(tab, Wp, a.Ms, a.interp, f0.rc.su, cu);
-            table_weights<W, R>(tab, Wp, a.Ms, a.interp, f0.rc.sv, cv);
-            C2 v = f0.v;
-            v.x *= f0.wt;
-            v.y *= f0.wt;
-            s_x0[lane] = xrel;
-            stage_shifted<W, R>(s_cv + lane, cv, rec_row(f0.rc.rx) - row0);
-#pragma unroll
-            for (int i = 0; i < W; ++i) {
-              C2 t;
-              t.x = cu[i] * v.x;
-              t.y = cu[i] * v.y;
-              s_a[lane * W + i] = t;
-            }
-            cover = cover_mask(xrel, W);
-          }
+          const int lo = cstart - wbase, hi = ce - wbase;
+          const bool mine = lane >= lo && lane < hi;
+          const int xrel = rec_xrel(f0.rc.rx);
+          if (mine) s_x0[lane] = xrel;
+          stage_chunk<W, R, true>(tab, Wp, a.Ms, a.interp, lo, hi, f0.rc.su, f0.rc.sv, rec_row(f0.rc.rx) - row0,
+                                  f0.v.x * f0.wt, f0.v.y * f0.wt, s_cv, s_a, lane);
+          const unsigned cover = mine ? cover_mask(xrel, W) : 0u;
           __syncwarp();
           unsigned M = transpose32(cover, lane);
           while (M) {
@@ -221,7 +263,7 @@ __device__ __forceinline__ void grid_item(const SweepArgs& a, const R* __restric
             const C2 ai = s_a[l * W + (lane - s_x0[l])];
 #pragma unroll
             for (int q = 0; q < TT; ++q) {
-              const R c = s_cv[q * 32 + l];
+              const R c = s_cv[q * Coop<W>::pitch + l];
               const int k = (gp * kD + q) % RS;
               if constexpr (kPk) {
                 acc2[k] = f2fma(f2pack(c, c), f2pack(ai.x, ai.y), acc2[k]);
@@ -366,19 +408,13 @@ __device__ __forceinline__ void degrid_item(const SweepArgs& a, const R* __restr
         const int re = off[min(row0 + kD, item.r1)];
         while (cstart < re) {
           const int ce = min(re, wbase + 32);
-          const bool mine = lane >= cstart - wbase && lane < ce - wbase;
+          const int lo = cstart - wbase, hi = ce - wbase;
+          const bool mine = lane >= lo && lane < hi;
           const int xrel = rec_xrel(rc0.rx);
-          unsigned cover = 0u;
-          if (mine) {
-            R cu[W], cv[W];
-            table_weights<W, R>(tab, Wp, a.Ms, a.interp, rc0.su, cu);
-            table_weights<W, R>(tab, Wp, a.Ms, a.interp, rc0.sv, cv);
-            s_x0[lane] = xrel;
-            stage_shifted<W, R>(s_cv + lane, cv, rec_row(rc0.rx) - row0);
-#pragma unroll
-            for (int j = 0; j < W; ++j) s_cu[lane * W + j] = cu[j];
-            cover = cover_mask(xrel, W);
-          }
+          if (mine) s_x0[lane] = xrel;
+          stage_chunk<W, R, false>(tab, Wp, a.Ms, a.interp, lo, hi, rc0.su, rc0.sv, rec_row(rc0.rx) - row0, R(0),
+                                   R(0), s_cv, s_cu, lane);
+          const unsigned cover = mine ? cover_mask(xrel, W) : 0u;
           __syncwarp();
           unsigned M = transpose32(cover, lane);
           while (M) {
@@ -390,7 +426,7 @@ __device__ __forceinline__ void degrid_item(const SweepArgs& a, const R* __restr
               unsigned long long s2 = 0ull;
 #pragma unroll
               for (int q = 0; q < TT; ++q) {
-                const R c = s_cv[q * 32 + l];
+                const R c = s_cv[q * Coop<W>::pitch + l];
                 s2 = f2fma(f2pack(c, c), g2[(gp * kD + q) % RS], s2);
               }
               const float2 f = f2unpack(s2);
@@ -399,7 +435,7 @@ __device__ __forceinline__ void degrid_item(const SweepArgs& a, const R* __restr
             } else {
 #pragma unroll
               for (int q = 0; q < TT; ++q) {
-                const R c = s_cv[q * 32 + l];
+                const R c = s_cv[q * Coop<W>::pitch + l];
                 sr = fma(c, g_re[(gp * kD + q) % RS], sr);
                 si = fma(c, g_im[(gp * kD + q) % RS], si);
               }
@@ -464,7 +500,8 @@ __device__ __forceinline__ void fixup_one(const VisPos* __restrict__ pos, long l
 inline size_t stage_bytes(int W, int dtype, bool degrid) {
   const size_t rs = dtype ? 8 : 4;
   const int T = W + kD - 1;
-  const size_t x0 = 32 * sizeof(int), cv = 32 * size_t(T) * rs, cu = 32 * size_t(W) * rs, ab = 32 * W * 2 * rs;
+  const size_t x0 = 32 * sizeof(int), cv = align16(size_t(T) * (32 + 32 / coop_group(W)) * rs),
+               cu = 32 * size_t(W) * rs, ab = 32 * W * 2 * rs;
   return align16(x0 + cv + (degrid ? cu : 0) + ab);
 }
 
