@@ -196,15 +196,25 @@ class Clocks:
                 "samples": len(sm)}
 
 
+SWEEP_SOURCES = ("sweep.cu", "sweep_body.cuh", "device_common.cuh")
+
+
+def sweep_sources_sha256():
+    h = hashlib.sha256()
+    for name in SWEEP_SOURCES:
+        with open(os.path.join(ROOT, "paper_1906_07102_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def traffic_record():
     """DRAM traffic of the gridding pass from the committed ncu summary, if it was taken
-    on the current sweep source."""
+    on the current sweep sources."""
     p = os.path.join(ROOT, "profiles", "grid_sweep_config2_traffic.json")
     try:
         with open(p) as f:
             rec = json.load(f)
-        src = open(os.path.join(ROOT, "paper_1906_07102_gb300", "csrc", "sweep.cu"), "rb").read()
-        if rec.get("sweep_cu_sha256") != hashlib.sha256(src).hexdigest():
+        if rec.get("sweep_sources_sha256") != sweep_sources_sha256():
             return None
         return float(rec["traffic_bytes_per_launch"])
     except (OSError, KeyError, ValueError):

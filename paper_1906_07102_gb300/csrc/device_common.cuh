@@ -101,31 +101,6 @@ __device__ __forceinline__ unsigned cover_mask(int xrel, int W) {
   return static_cast<unsigned>(m);
 }
 
-// Table lookup (Section 5.1, Appendix F). Row k and fraction f come from the exact
-// integer product S * Ms (S in units of 2^-32): linear uses k = floor(t), f = t - k with
-// t = S Ms 2^-32; nearest uses row floor(t + 1/2). The table has Ms+1 rows of stride Wp.
-template <int W, typename R>
-__device__ __forceinline__ void table_weights(const R* __restrict__ tab, int Wp, int Ms, int interp,
-                                              unsigned S, R (&C)[W]) {
-  const unsigned long long P = static_cast<unsigned long long>(S) * static_cast<unsigned>(Ms);
-  if (interp) {
-    const int k = static_cast<int>(P >> 32);
-    const R f = static_cast<R>(static_cast<unsigned>(P & 0xffffffffull)) * static_cast<R>(2.3283064365386962890625e-10);
-    const R* r0 = tab + static_cast<size_t>(k) * Wp;
-    const R* r1 = r0 + Wp;
-#pragma unroll
-    for (int j = 0; j < W; ++j) {
-      const R a = r0[j];
-      C[j] = a + f * (r1[j] - a);
-    }
-  } else {
-    const int k = static_cast<int>((P + 0x80000000ull) >> 32);
-    const R* r0 = tab + static_cast<size_t>(k) * Wp;
-#pragma unroll
-    for (int j = 0; j < W; ++j) C[j] = r0[j];
-  }
-}
-
 // Packed single-precision pairs (re, im) in one 64-bit register: Blackwell's f32x2 FMA
 // does a complex-by-real multiply-add in one instruction.
 __device__ __forceinline__ unsigned long long f2pack(float x, float y) {

@@ -79,38 +79,43 @@ template <int W, typename R> struct Stage {
   static constexpr size_t degrid_bytes = x0_bytes + cv_bytes + cu_bytes + a_bytes;
 };
 
-// Interpolated table entry i at coordinate S (the arithmetic of table_weights, one entry).
+// Table lookup (Section 5.1, Appendix F): row offset (elements) and interpolation fraction
+// of coordinate S (units of 2^-32), from the exact integer product S Ms. Linear uses row
+// k = floor(t) and fraction t - k with t = S Ms 2^-32; nearest uses row floor(t + 1/2). The
+// table has Ms + 1 rows of stride Wp.
 template <typename R>
-__device__ __forceinline__ R table_entry(const R* __restrict__ tab, int Wp, int Ms, int interp, unsigned S, int i) {
+__device__ __forceinline__ void table_coord(int Wp, int Ms, int interp, unsigned S, int& off, R& f) {
   const unsigned long long Pm = static_cast<unsigned long long>(S) * static_cast<unsigned>(Ms);
   if (interp) {
-    const int k = static_cast<int>(Pm >> 32);
-    const R f = static_cast<R>(static_cast<unsigned>(Pm & 0xffffffffull)) * static_cast<R>(2.3283064365386962890625e-10);
-    const R* r0 = tab + static_cast<size_t>(k) * Wp;
-    const R a0 = r0[i];
-    return a0 + f * (r0[Wp + i] - a0);
+    off = static_cast<int>(Pm >> 32) * Wp;
+    f = static_cast<R>(static_cast<unsigned>(Pm & 0xffffffffull)) * static_cast<R>(2.3283064365386962890625e-10);
+  } else {
+    off = static_cast<int>((Pm + 0x80000000ull) >> 32) * Wp;
+    f = R(0);
   }
-  const int k = static_cast<int>((Pm + 0x80000000ull) >> 32);
-  return tab[static_cast<size_t>(k) * Wp + i];
 }
 
-// Stages the weights of a chunk's records, held one per lane by lanes lo .. hi-1 (su, sv,
-// row offset d in the group, and for gridding w V): Cv shifted by d into s_cv (entry q of
-// record l at q * pitch + l, zero for q outside [d, d + W)) and Cu, times w V when
-// gridding, into s_u[l * W + i]. G lanes share a record and compute one table entry each,
-// so a round's table reads touch P rows instead of 32 rows per instruction.
+// Stages the weights of a chunk's records, held one per lane by lanes lo .. hi-1 (table
+// row offsets and fractions for u and v, row offset d in the group, and for gridding
+// w V): Cv shifted by d into s_cv (entry q of record l at q * pitch + l, zero for q
+// outside [d, d + W)) and Cu, times w V when gridding, into s_u[l * W + i]. G lanes share
+// a record and compute one table entry each (C = T[k] + f (T[k+1] - T[k])), so a round's
+// table reads touch P rows instead of 32 rows per instruction.
 template <int W, typename R, bool GRID>
-__device__ __forceinline__ void stage_chunk(const R* __restrict__ tab, int Wp, int Ms, int interp, int lo, int hi,
-                                            unsigned su, unsigned sv, int d, R wx, R wy, R* __restrict__ s_cv,
+__device__ __forceinline__ void stage_chunk(const R* __restrict__ tab, int Wp, int interp, int lo, int hi, int ou,
+                                            R fu, int ov, R fv, int d, R wx, R wy, R* __restrict__ s_cv,
                                             void* __restrict__ s_u, int lane) {
   using C2 = typename Cplx<R>::T;
   constexpr int G = Coop<W>::G, P = Coop<W>::P, pitch = Coop<W>::pitch, TT = Ring<W>::T;
   const int g = lane / G, i = lane % G;
+  const int ovd = ov | (d << 28);  // row offsets stay below 2^28 (Ms <= 10^6, Wp <= 16)
   for (int r0 = lo; r0 < hi; r0 += P) {
     const int r = r0 + g, src = r & 31;
-    const unsigned su_r = __shfl_sync(0xffffffffu, su, src);
-    const unsigned sv_r = __shfl_sync(0xffffffffu, sv, src);
-    const int d_r = __shfl_sync(0xffffffffu, d, src);
+    const int ou_r = __shfl_sync(0xffffffffu, ou, src);
+    const R fu_r = __shfl_sync(0xffffffffu, fu, src);
+    const int ovd_r = __shfl_sync(0xffffffffu, ovd, src);
+    const R fv_r = __shfl_sync(0xffffffffu, fv, src);
+    const int ov_r = ovd_r & 0x0fffffff, d_r = ovd_r >> 28;
     R wx_r = R(0), wy_r = R(0);
     if constexpr (GRID) {
       wx_r = __shfl_sync(0xffffffffu, wx, src);
@@ -118,8 +123,11 @@ __device__ __forceinline__ void stage_chunk(const R* __restrict__ tab, int Wp, i
     }
     if (r < hi) {
       if (i < W) {
-        const R cu = table_entry<R>(tab, Wp, Ms, interp, su_r, i);
-        const R cv = table_entry<R>(tab, Wp, Ms, interp, sv_r, i);
+        R cu = tab[ou_r + i], cv = tab[ov_r + i];
+        if (interp) {
+          cu = cu + fu_r * (tab[ou_r + Wp + i] - cu);
+          cv = cv + fv_r * (tab[ov_r + Wp + i] - cv);
+        }
         if constexpr (GRID) {
           C2 t;
           t.x = cu * wx_r;
@@ -130,7 +138,8 @@ __device__ __forceinline__ void stage_chunk(const R* __restrict__ tab, int Wp, i
         }
         s_cv[(i + d_r) * pitch + r] = cv;
       }
-      for (int z = i; z < TT - W; z += G) s_cv[(z < d_r ? z : z + W) * pitch + r] = R(0);
+      // the kD - 1 zero entries, on the group's spare lanes where it has them
+      for (int z = (i - W + G) % G; z < TT - W; z += G) s_cv[(z < d_r ? z : z + W) * pitch + r] = R(0);
     }
   }
 }
@@ -192,7 +201,6 @@ __device__ __forceinline__ void grid_item(const SweepArgs& a, const R* __restric
   using St = Stage<W, R>;
   constexpr int Wp = wpad<R>(W);
   constexpr int RS = Ring<W>::R, P = Ring<W>::P, TT = Ring<W>::T;
-  constexpr bool kPk = sizeof(R) == 4 && !COMP;
   int* s_x0 = reinterpret_cast<int*>(my);
   R* s_cv = reinterpret_cast<R*>(my + St::x0_bytes);
   C2* s_a = reinterpret_cast<C2*>(my + St::x0_bytes + St::cv_bytes);
@@ -218,14 +226,12 @@ __device__ __forceinline__ void grid_item(const SweepArgs& a, const R* __restric
   const int* __restrict__ off = a.offsets + static_cast<long long>(item.strip) * N;
   const int col = item.strip * kStrip + lane;
   const int nrows = item.r1 - item.r0;
-  // ring slot x % RS accumulates relative row x of column `col` (packed (re, im) pairs on
-  // the plain float32 path, separate real arrays otherwise)
+  // ring slot x % RS accumulates relative row x of column `col` (separate real and
+  // imaginary arrays: two scalar FMAs measured faster here than one packed f32x2 FMA)
   R acc_re[RS], acc_im[RS], lo_re[RS], lo_im[RS];
-  unsigned long long acc2[RS];
 #pragma unroll
   for (int q = 0; q < RS; ++q) {
     acc_re[q] = acc_im[q] = lo_re[q] = lo_im[q] = R(0);
-    acc2[q] = 0ull;
   }
   // software pipeline over 32-record windows of the item (window k = records
   // rb + 32k .. rb + 32k + 31, lane l holding record rb + 32k + l): while window k is
@@ -252,7 +258,11 @@ __device__ __forceinline__ void grid_item(const SweepArgs& a, const R* __restric
           const bool mine = lane >= lo && lane < hi;
           const int xrel = rec_xrel(f0.rc.rx);
           if (mine) s_x0[lane] = xrel;
-          stage_chunk<W, R, true>(tab, Wp, a.Ms, a.interp, lo, hi, f0.rc.su, f0.rc.sv, rec_row(f0.rc.rx) - row0,
+          int ou, ov;
+          R fu, fv;
+          table_coord<R>(Wp, a.Ms, a.interp, f0.rc.su, ou, fu);
+          table_coord<R>(Wp, a.Ms, a.interp, f0.rc.sv, ov, fv);
+          stage_chunk<W, R, true>(tab, Wp, a.interp, lo, hi, ou, fu, ov, fv, rec_row(f0.rc.rx) - row0,
                                   f0.v.x * f0.wt, f0.v.y * f0.wt, s_cv, s_a, lane);
           const unsigned cover = mine ? cover_mask(xrel, W) : 0u;
           __syncwarp();
@@ -265,9 +275,7 @@ __device__ __forceinline__ void grid_item(const SweepArgs& a, const R* __restric
             for (int q = 0; q < TT; ++q) {
               const R c = s_cv[q * Coop<W>::pitch + l];
               const int k = (gp * kD + q) % RS;
-              if constexpr (kPk) {
-                acc2[k] = f2fma(f2pack(c, c), f2pack(ai.x, ai.y), acc2[k]);
-              } else if constexpr (COMP) {
+              if constexpr (COMP) {
                 two_sum_acc(acc_re[k], lo_re[k], c * ai.x);
                 two_sum_acc(acc_im[k], lo_im[k], c * ai.y);
               } else {
@@ -292,11 +300,7 @@ __device__ __forceinline__ void grid_item(const SweepArgs& a, const R* __restric
           const int k = (gp * kD + d) % RS;
           if (gb + d < nrows) {
             C2 o;
-            if constexpr (kPk) {
-              const float2 f = f2unpack(acc2[k]);
-              o.x = f.x;
-              o.y = f.y;
-            } else if constexpr (COMP) {
+            if constexpr (COMP) {
               o.x = acc_re[k] + lo_re[k];
               o.y = acc_im[k] + lo_im[k];
             } else {
@@ -305,7 +309,6 @@ __device__ __forceinline__ void grid_item(const SweepArgs& a, const R* __restric
             }
             grid[static_cast<size_t>(row0 + d) * N + col] = o;
             acc_re[k] = acc_im[k] = lo_re[k] = lo_im[k] = R(0);
-            acc2[k] = 0ull;
           }
         }
       }
@@ -317,11 +320,7 @@ __device__ __forceinline__ void grid_item(const SweepArgs& a, const R* __restric
 #pragma unroll
   for (int q = 0; q < RS; ++q) {
     C2 o;
-    if constexpr (kPk) {
-      const float2 f = f2unpack(acc2[q]);
-      o.x = f.x;
-      o.y = f.y;
-    } else if constexpr (COMP) {
+    if constexpr (COMP) {
       o.x = acc_re[q] + lo_re[q];
       o.y = acc_im[q] + lo_im[q];
     } else {
@@ -412,8 +411,12 @@ __device__ __forceinline__ void degrid_item(const SweepArgs& a, const R* __restr
           const bool mine = lane >= lo && lane < hi;
           const int xrel = rec_xrel(rc0.rx);
           if (mine) s_x0[lane] = xrel;
-          stage_chunk<W, R, false>(tab, Wp, a.Ms, a.interp, lo, hi, rc0.su, rc0.sv, rec_row(rc0.rx) - row0, R(0),
-                                   R(0), s_cv, s_cu, lane);
+          int ou, ov;
+          R fu, fv;
+          table_coord<R>(Wp, a.Ms, a.interp, rc0.su, ou, fu);
+          table_coord<R>(Wp, a.Ms, a.interp, rc0.sv, ov, fv);
+          stage_chunk<W, R, false>(tab, Wp, a.interp, lo, hi, ou, fu, ov, fv, rec_row(rc0.rx) - row0, R(0), R(0),
+                                   s_cv, s_cu, lane);
           const unsigned cover = mine ? cover_mask(xrel, W) : 0u;
           __syncwarp();
           unsigned M = transpose32(cover, lane);
