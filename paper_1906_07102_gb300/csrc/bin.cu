@@ -1,13 +1,16 @@
 // Binning of visibility positions (support rule of Eq. 6) into 32-column strips sorted
-// by support-start row, and balanced work items for the sweep kernels.
+// by pairs of support-start rows, and balanced work items for the sweep kernels.
 //
 // Pipeline (all on one stream, no host synchronisation):
 //   1. k_bin_count   per visibility: float64 product to cells, exact fixed-point support
 //                    rule, strip keys (one, or two when the support crosses into the next
 //                    strip); the bucket counter's returned value is the record's rank.
 //   2. scan          exclusive prefix sum of the bucket counts (strip-major, row-minor).
-//   3. k_bin_scatter records to offset + rank (order inside a bucket is arbitrary).
-//   4. k_make_items  per strip and block of rows: items holding about item_target records.
+//   3. k_bin_scatter records of each pair of rows (2m, 2m+1) of a strip -- the row group
+//                    the sweeps stage together -- to the pair's range, dealt so that any
+//                    32 consecutive records sample the whole pair (see dealt_position).
+//   4. k_make_items  per strip and block of rows: items holding about item_target records,
+//                    cut at even rows so that the sweeps' row groups are these pairs.
 #include <cuda_runtime.h>
 
 #include "device_common.cuh"
@@ -166,6 +169,20 @@ __global__ void k_scan_final(const int* __restrict__ in, long long n, const int*
 }
 
 // Pass 2: every record to offsets[bucket] + rank (no atomics).
+// Position of the record of rank rho (0 .. n-1, in arrival order) inside its row pair of
+// n records. Records of one baseline arrive in time order and land in nearby cells, so
+// consecutive ranks cluster on a few columns; the sweeps give each lane the records that
+// cover its column, so a chunk of clustered records leaves most lanes idle. The pair is
+// dealt into nc = ceil(n / 32) runs, run j holding the ranks j, j + nc, j + 2 nc, ...
+// (q or q + 1 of them, q = n / nc), so that any 32 consecutive positions hold ranks
+// spread over the whole pair.
+__device__ __forceinline__ int dealt_position(int rho, int n) {
+  if (n <= 32) return rho;
+  const int nc = (n + 31) >> 5, q = n / nc, r = n - q * nc;
+  const int j = rho % nc;
+  return j * q + min(j, r) + rho / nc;
+}
+
 __global__ void k_bin_scatter(const VisPos* __restrict__ pos, const int2* __restrict__ rank, long long nvis,
                               int W, int N, int n_strips, const int* __restrict__ offsets,
                               Rec* __restrict__ recs) {
@@ -175,10 +192,18 @@ __global__ void k_bin_scatter(const VisPos* __restrict__ pos, const int2* __rest
     if (vp.x0 < 0) continue;
     const int2 rk = rank[k];
     const int strip = vp.x0 / kStrip, xr = vp.x0 % kStrip;
-    recs[offsets[strip * N + vp.y0] + rk.x] = Rec{static_cast<unsigned>(k), rec_pack(vp.y0, xr), vp.su, vp.sv};
+    const int odd = vp.y0 & 1;
+    // row pair (y0 & ~1, y0 | 1) of the strip: [offsets[g], offsets[g + 2])
+    const int* og = offsets + strip * N + (vp.y0 - odd);
+    int gs = og[0];
+    recs[gs + dealt_position((odd ? og[1] - gs : 0) + rk.x, og[2] - gs)] =
+        Rec{static_cast<unsigned>(k), rec_pack(vp.y0, xr), vp.su, vp.sv};
     if (xr + W > kStrip) {
       const int s2 = (strip + 1) % n_strips;
-      recs[offsets[s2 * N + vp.y0] + rk.y] = Rec{static_cast<unsigned>(k), rec_pack(vp.y0, xr - kStrip), vp.su, vp.sv};
+      og = offsets + s2 * N + (vp.y0 - odd);
+      gs = og[0];
+      recs[gs + dealt_position((odd ? og[1] - gs : 0) + rk.y, og[2] - gs)] =
+          Rec{static_cast<unsigned>(k), rec_pack(vp.y0, xr - kStrip), vp.su, vp.sv};
     }
   }
 }
@@ -213,7 +238,7 @@ __global__ void k_make_items(const int* __restrict__ offsets, int N, int n_strip
       if (s_off[mid] >= goal) hi = mid;
       else lo = mid + 1;
     }
-    return lo;
+    return lo & ~1;  // even rows: the sweeps' row groups are the binned row pairs
   };
   for (int k = threadIdx.x; k < m; k += blockDim.x) {
     const int r0 = cut(k), r1 = cut(k + 1);

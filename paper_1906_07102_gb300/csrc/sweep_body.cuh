@@ -3,8 +3,10 @@
 // persistent kernels (batch.cu).
 //
 // The grid is cut into 32-column strips; a warp owns one work item (a range of rows of
-// one strip) and lane t owns column t of the strip. The item's records are sorted by
-// support-start row and visited in groups of kD = 2 rows, in chunks of up to 32 records
+// one strip) and lane t owns column t of the strip. The item's records come grouped by
+// pairs of support-start rows (dealt inside a pair by the binning, so that 32 consecutive
+// records spread over the pair's columns) and are visited in groups of kD = 2 rows, in
+// chunks of up to 32 records
 // (the records and visibilities of the next two chunks are already in flight):
 //   1. the chunk's 2W table weights per record (Section 5.1 lookup) are staged in shared
 //      memory: Cu_i w V (gridding) or Cu_i (degridding), and Cv_j shifted by the record's
@@ -47,7 +49,7 @@ template <typename R> __host__ __device__ constexpr int wpad(int W) {
 
 // Rows per group and the register ring: RS >= T = W + kD - 1 slots, a multiple of kD, so
 // that the group loop unrolled over P = RS / kD groups indexes every slot at compile time.
-constexpr int kD = 2;
+constexpr int kD = 2;  // the binning's row pairs (bin.cu) are these groups
 template <int W> struct Ring {
   static constexpr int T = W + kD - 1;
   static constexpr int R = kD * ((T + kD - 1) / kD);
@@ -267,6 +269,26 @@ __device__ __forceinline__ void grid_item(const SweepArgs& a, const R* __restric
           const unsigned cover = mine ? cover_mask(xrel, W) : 0u;
           __syncwarp();
           unsigned M = transpose32(cover, lane);
+          if constexpr (!COMP) {
+            while (M) {
+              const int l1 = __ffs(M) - 1;
+              M &= M - 1u;
+              const bool two = M != 0u;
+              const int l2 = two ? __ffs(M) - 1 : l1;
+              if (two) M &= M - 1u;
+              const C2 a1 = s_a[l1 * W + (lane - s_x0[l1])];
+              C2 a2 = s_a[l2 * W + (lane - s_x0[l2])];
+              if (!two) { a2.x = R(0); a2.y = R(0); }
+#pragma unroll
+              for (int q = 0; q < TT; ++q) {
+                const R c1 = s_cv[q * Coop<W>::pitch + l1];
+                const R c2 = s_cv[q * Coop<W>::pitch + l2];
+                const int k = (gp * kD + q) % RS;
+                acc_re[k] = fma(c1, a1.x, fma(c2, a2.x, acc_re[k]));
+                acc_im[k] = fma(c1, a1.y, fma(c2, a2.y, acc_im[k]));
+              }
+            }
+          }
           while (M) {
             const int l = __ffs(M) - 1;
             M &= M - 1u;
@@ -420,6 +442,33 @@ __device__ __forceinline__ void degrid_item(const SweepArgs& a, const R* __restr
           const unsigned cover = mine ? cover_mask(xrel, W) : 0u;
           __syncwarp();
           unsigned M = transpose32(cover, lane);
+          if constexpr (kPk) {
+            while (M) {
+              const int l1 = __ffs(M) - 1;
+              M &= M - 1u;
+              const bool two = M != 0u;
+              const int l2 = two ? __ffs(M) - 1 : l1;
+              if (two) M &= M - 1u;
+              const int i1 = lane - s_x0[l1], i2 = lane - s_x0[l2];
+              unsigned long long s1 = 0ull, s2 = 0ull;
+#pragma unroll
+              for (int q = 0; q < TT; ++q) {
+                const R c1 = s_cv[q * Coop<W>::pitch + l1];
+                const R c2 = s_cv[q * Coop<W>::pitch + l2];
+                s1 = f2fma(f2pack(c1, c1), g2[(gp * kD + q) % RS], s1);
+                s2 = f2fma(f2pack(c2, c2), g2[(gp * kD + q) % RS], s2);
+              }
+              const float2 f1 = f2unpack(s1), f2 = f2unpack(s2);
+              const R cu1 = s_cu[l1 * W + i1], cu2 = s_cu[l2 * W + i2];
+              C2 p1, p2;
+              p1.x = cu1 * f1.x;
+              p1.y = cu1 * f1.y;
+              p2.x = cu2 * f2.x;
+              p2.y = cu2 * f2.y;
+              s_p[l1 * W + i1] = p1;
+              if (two) s_p[l2 * W + i2] = p2;
+            }
+          }
           while (M) {
             const int l = __ffs(M) - 1;
             M &= M - 1u;
