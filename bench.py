@@ -340,10 +340,10 @@ def run_native(args):
     work = torch.empty((w["N"], w["N"]), dtype=torch.complex64, device=dev)
     timed("bin", lambda: plan.bin(uv_d))
     timed("grid", lambda: plan.grid(vis_d, out=work))
-    timed("fft_image", lambda: plan.fft(work, "image"))
+    timed("fft_image", lambda: plan.fft(work, "image", pruned=True))
     timed("crop_correct", lambda: plan.crop_correct(work, out=img_d))
     timed("pad_correct", lambda: plan.pad_correct(model_d, out=work))
-    timed("fft_model", lambda: plan.fft(work, "model"))
+    timed("fft_model", lambda: plan.fft(work, "model", pruned=True))
     timed("degrid", lambda: plan.degrid(work, out=pv_d))
 
     # end to end through the public API with pinned host buffers

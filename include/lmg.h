@@ -163,6 +163,16 @@ int lmg_degrid(lmg_plan* p, const void* grid, void* vis_out, void* stream);
  * LMG_FFT_MODEL computes sum_q P[q] exp(-i 2 pi i q / N) (cuFFT forward). */
 int lmg_fft(lmg_plan* p, int direction, void* grid, void* stream);
 
+/* lmg_fft_pruned -- the transform lmg_dirty_image (LMG_FFT_IMAGE) or lmg_predict_vis
+ * (LMG_FFT_MODEL) applies to the work grid, in place on `grid` ([N][N], plan dtype). Only
+ * the kept field of Eq. 4 (|x| <= x0 / 2, n_image pixels per axis) is needed there, so:
+ * LMG_FFT_IMAGE transforms every row, then only the n_image kept columns (index q mod N in
+ * [0, n_image/2) or [N - n_image/2, N)); its result equals lmg_fft's at the kept rows and
+ * columns and is partial elsewhere. LMG_FFT_MODEL transforms only the n_image kept rows,
+ * then every column; its result equals lmg_fft's when every other row is zero (as after
+ * lmg_grid_correct with LMG_PAD). */
+int lmg_fft_pruned(lmg_plan* p, int direction, void* grid, void* stream);
+
 /* lmg_grid_correct -- grid correction and crop (Eqs. 4, 15), or its adjoint.
  *   LMG_CROP: in = FFT output [N][N] of a grid in index order, out = image
  *             [n_image][n_image] with out[p][q] = h(y_p) h(x_q) F(x_q, y_p).
@@ -186,7 +196,9 @@ int lmg_predict_vis(lmg_plan* p, const void* image, void* vis_out, void* stream)
 int lmg_plan_info(lmg_plan* p, int64_t* out, void* stream);
 
 /* lmg_work_grid -- device pointer of the plan's internal [N][N] work grid (valid until
- * lmg_plan_free); holds the FFT-domain grid after lmg_dirty_image / lmg_predict_vis. */
+ * lmg_plan_free). lmg_dirty_image and lmg_predict_vis transform it with FFTs pruned to
+ * the outputs they use: afterwards it holds the transform at the kept rows and columns
+ * (dirty image) or the full model grid (prediction). */
 void* lmg_work_grid(lmg_plan* p);
 
 /* lmg_grid_static -- binning plus gridding (the work of lmg_plan_bin + lmg_grid, complex64)

@@ -70,6 +70,12 @@ void free_plan(lmg_plan* p) {
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->fft_ok) cufftDestroy(p->fft);
+  if (p->fft_pruned_ok) {
+    cufftDestroy(p->fft_rows_all);
+    cufftDestroy(p->fft_rows_half);
+    cufftDestroy(p->fft_cols_all);
+    cufftDestroy(p->fft_cols_half);
+  }
   delete p;
 }
 
@@ -144,6 +150,42 @@ int do_fft(lmg_plan* p, int direction, void* g, cudaStream_t st) {
     r = cufftExecC2C(p->fft, static_cast<cufftComplex*>(g), static_cast<cufftComplex*>(g), dir);
   if (r != CUFFT_SUCCESS) return set_error(LMG_ECUFFT, "cuFFT execution failed (code " + std::to_string(int(r)) + ")");
   return LMG_OK;
+}
+
+// Pruned transforms (Eq. 4 keeps |x| <= x0 / 2 only). The dirty image needs the outputs of
+// the kept columns and rows alone: row transforms of every row, then column transforms of
+// the n_image kept columns (q mod N in [0, n/2) and [N - n/2, N)). The model grid has
+// non-zero input rows only at the kept rows: row transforms of those n_image rows, then
+// column transforms of every column. Same sums as the full 2-D transform on the outputs
+// that are used; the other outputs of the work grid are left partially transformed.
+int exec_1d(lmg_plan* p, cufftHandle h, void* g, size_t offset, int dir, cudaStream_t st) {
+  if (cufftSetStream(h, st) != CUFFT_SUCCESS) return set_error(LMG_ECUFFT, "cufftSetStream failed");
+  cufftResult r;
+  if (p->dtype == LMG_C128) {
+    auto* d = static_cast<cufftDoubleComplex*>(g) + offset;
+    r = cufftExecZ2Z(h, d, d, dir);
+  } else {
+    auto* d = static_cast<cufftComplex*>(g) + offset;
+    r = cufftExecC2C(h, d, d, dir);
+  }
+  if (r != CUFFT_SUCCESS) return set_error(LMG_ECUFFT, "cuFFT execution failed (code " + std::to_string(int(r)) + ")");
+  return LMG_OK;
+}
+
+int fft_image_pruned(lmg_plan* p, void* g, cudaStream_t st) {
+  const size_t N = size_t(p->N), half = size_t(p->n_image / 2);
+  int rc = exec_1d(p, p->fft_rows_all, g, 0, CUFFT_INVERSE, st);
+  if (rc == LMG_OK) rc = exec_1d(p, p->fft_cols_half, g, 0, CUFFT_INVERSE, st);
+  if (rc == LMG_OK) rc = exec_1d(p, p->fft_cols_half, g, N - half, CUFFT_INVERSE, st);
+  return rc;
+}
+
+int fft_model_pruned(lmg_plan* p, void* g, cudaStream_t st) {
+  const size_t N = size_t(p->N), half = size_t(p->n_image / 2);
+  int rc = exec_1d(p, p->fft_rows_half, g, 0, CUFFT_FORWARD, st);
+  if (rc == LMG_OK) rc = exec_1d(p, p->fft_rows_half, g, (N - half) * N, CUFFT_FORWARD, st);
+  if (rc == LMG_OK) rc = exec_1d(p, p->fft_cols_all, g, 0, CUFFT_FORWARD, st);
+  return rc;
 }
 
 }  // namespace
@@ -264,6 +306,22 @@ int plan_create(const lmg_table* t, int64_t n_image, double pixel_scale, int64_t
                        "cufftPlan2d failed (code " + std::to_string(int(fr)) + ")");
     }
     p->fft_ok = true;
+    // pruned 1-D batches for the imaging and prediction paths
+    int n1 = int(N), half = int(n_image / 2);
+    const cufftType ty = dtype == LMG_C128 ? CUFFT_Z2Z : CUFFT_C2C;
+    cufftResult r1 = cufftPlanMany(&p->fft_rows_all, 1, &n1, nullptr, 1, n1, nullptr, 1, n1, ty, n1);
+    cufftResult r2 = cufftPlanMany(&p->fft_rows_half, 1, &n1, nullptr, 1, n1, nullptr, 1, n1, ty, half);
+    cufftResult r3 = cufftPlanMany(&p->fft_cols_all, 1, &n1, &n1, n1, 1, &n1, n1, 1, ty, n1);
+    cufftResult r4 = cufftPlanMany(&p->fft_cols_half, 1, &n1, &n1, n1, 1, &n1, n1, 1, ty, half);
+    if (r1 != CUFFT_SUCCESS || r2 != CUFFT_SUCCESS || r3 != CUFFT_SUCCESS || r4 != CUFFT_SUCCESS) {
+      if (r1 == CUFFT_SUCCESS) cufftDestroy(p->fft_rows_all);
+      if (r2 == CUFFT_SUCCESS) cufftDestroy(p->fft_rows_half);
+      if (r3 == CUFFT_SUCCESS) cufftDestroy(p->fft_cols_all);
+      if (r4 == CUFFT_SUCCESS) cufftDestroy(p->fft_cols_half);
+      free_plan(p);
+      return set_error(LMG_ECUFFT, "cufftPlanMany failed");
+    }
+    p->fft_pruned_ok = true;
   }
   *out = p;
   return LMG_OK;
@@ -480,6 +538,15 @@ int lmg_fft(lmg_plan* p, int direction, void* grid, void* stream) {
   return do_fft(p, direction, grid, static_cast<cudaStream_t>(stream));
 }
 
+int lmg_fft_pruned(lmg_plan* p, int direction, void* grid, void* stream) {
+  clear_error();
+  if (!p || !grid) return set_error(LMG_EINVAL, "NULL argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (direction == LMG_FFT_IMAGE) return fft_image_pruned(p, grid, st);
+  if (direction == LMG_FFT_MODEL) return fft_model_pruned(p, grid, st);
+  return set_error(LMG_EINVAL, "bad direction");
+}
+
 int lmg_grid_correct(lmg_plan* p, int direction, const void* in, void* out, void* stream) {
   clear_error();
   if (!p || !in || !out) return set_error(LMG_EINVAL, "NULL argument");
@@ -501,7 +568,7 @@ int lmg_dirty_image(lmg_plan* p, const void* vis, const void* weights, int accum
     return set_error(LMG_EUNSUPPORTED, "compensated accumulation is for LMG_C64");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int rc = do_grid(p, vis, weights, accum, p->work, st);
-  if (rc == LMG_OK) rc = do_fft(p, LMG_FFT_IMAGE, p->work, st);
+  if (rc == LMG_OK) rc = fft_image_pruned(p, p->work, st);
   if (rc == LMG_OK)
     rc = launch_status(crop_correct_launch(p->work, image_out, p->d_h, int(p->n_image), int(p->N), p->dtype, st),
                        "crop");
@@ -515,7 +582,7 @@ int lmg_predict_vis(lmg_plan* p, const void* image, void* vis_out, void* stream)
   if (p->nvis > 0 && !vis_out) return set_error(LMG_EINVAL, "vis_out is NULL");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int rc = launch_status(pad_correct_launch(image, p->work, p->d_h, int(p->n_image), int(p->N), p->dtype, st), "pad");
-  if (rc == LMG_OK) rc = do_fft(p, LMG_FFT_MODEL, p->work, st);
+  if (rc == LMG_OK) rc = fft_model_pruned(p, p->work, st);
   if (rc == LMG_OK) rc = do_degrid(p, p->work, vis_out, st);
   return rc;
 }

@@ -74,8 +74,12 @@ struct lmg_plan {
   void* spill = nullptr;
   void* dpart = nullptr;
   void* work = nullptr;      // N x N work grid (null in batch channels)
-  cufftHandle fft = 0;
+  cufftHandle fft = 0;              // full 2-D transform (lmg_fft)
   bool fft_ok = false;
+  // pruned transforms of lmg_dirty_image / lmg_predict_vis: 1-D batches over all rows,
+  // the n_image / 2 rows at either end, all columns, the n_image / 2 columns at either end
+  cufftHandle fft_rows_all = 0, fft_rows_half = 0, fft_cols_all = 0, fft_cols_half = 0;
+  bool fft_pruned_ok = false;
 };
 
 namespace lmg {

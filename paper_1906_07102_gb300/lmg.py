@@ -39,6 +39,7 @@ _SIGS = {
     "lmg_grid": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, _vp]),
     "lmg_degrid": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "lmg_fft": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
+    "lmg_fft_pruned": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     "lmg_grid_correct": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
     "lmg_dirty_image": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, _vp]),
     "lmg_predict_vis": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -191,9 +192,12 @@ class Plan:
         _check(lib().lmg_degrid(self._h, _ptr(grid), _ptr(out), _stream()))
         return out
 
-    def fft(self, grid, direction):
+    def fft(self, grid, direction, pruned=False):
+        """In-place 2-D FFT of an [N, N] grid; pruned=True runs the transform the imaging /
+        prediction paths use (exact on the kept field only, see lmg_fft_pruned)."""
         _need(grid, self.cdtype, (self.N, self.N), "grid")
-        _check(lib().lmg_fft(self._h, FFT_IMAGE if direction == "image" else FFT_MODEL, _ptr(grid), _stream()))
+        f = lib().lmg_fft_pruned if pruned else lib().lmg_fft
+        _check(f(self._h, FFT_IMAGE if direction == "image" else FFT_MODEL, _ptr(grid), _stream()))
         return grid
 
     def crop_correct(self, F, out=None):

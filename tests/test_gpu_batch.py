@@ -5,8 +5,11 @@ The channels differ in support width (W = 4, 6, 8 and 11, so that several persis
 launches share one graph), grid size (256^2 .. 1024^2), visibility count (0 to 60,000,
 ragged) and weighting. A batch runs the same per-item sweep code as a single plan; only
 the order of float32 sums inside one bucket may differ (record ranks come from atomic
-counters), so grids agree per element within 1e-5 of the largest cell and 1e-6 in
-relative RMS; one channel is also checked against the oracle at the float32 target 1e-5.
+counters), so grids and degridded visibilities agree per element within 1e-5 of the
+largest value and 1e-6 in relative RMS. Dirty images and predictions also pass through
+FFTs, which the batch runs as full batched 2-D transforms and a single plan as pruned 1-D
+transforms (different rounding), so those agree to the float32 target, 1e-5. One channel is
+also checked against the oracle at 1e-5.
 """
 import ctypes
 
@@ -28,11 +31,11 @@ CHANNELS = [(4, 512, 20000, False), (6, 256, 3001, True), (8, 1024, 60000, False
 MS = 1000
 
 
-def close(out, ref):
+def close(out, ref, rms=1e-6):
     scale = max(np.abs(ref).max(), 1e-30)
     assert np.abs(out - ref).max() <= 1e-5 * scale
     if np.abs(ref).max() > 0:
-        assert rel_rms(out, ref) <= 1e-6
+        assert rel_rms(out, ref) <= rms
 
 
 @pytest.fixture(scope="module")
@@ -91,9 +94,9 @@ def test_batch_dirty_image_and_predict(setup):
               for i, c in enumerate(CHANNELS)]
     pred = batch.predict_vis(models)
     for c, p in enumerate(plans):
-        close(imgs[c].cpu().numpy(), p.dirty_image(viss[c], wts[c]).cpu().numpy())
+        close(imgs[c].cpu().numpy(), p.dirty_image(viss[c], wts[c]).cpu().numpy(), rms=1e-5)
         if CHANNELS[c][2]:
-            close(pred[c].cpu().numpy(), p.predict_vis(models[c]).cpu().numpy())
+            close(pred[c].cpu().numpy(), p.predict_vis(models[c]).cpu().numpy(), rms=1e-5)
 
 
 def test_batch_channel_against_oracle(setup):

@@ -189,6 +189,22 @@ def test_fp32_fft_and_correction_stages(c2):
     assert rel_rms(img, ref_img) < 1e-5
 
 
+def test_pruned_ffts_match_full_fft_on_the_kept_field(c2):
+    """lmg_fft_pruned: equal to the full transform at the kept rows and columns (imaging),
+    and on a padded model grid (prediction)."""
+    uv, dl, vis, p, T, hv, op = c2
+    q = (np.arange(n2) - n2 // 2) % N2
+    G = to_dev(S.random_image(N2, 11).astype(np.complex64), torch.complex64)
+    full = p.fft(G.clone(), "image").cpu().numpy()[np.ix_(q, q)]
+    pruned = p.fft(G.clone(), "image", pruned=True).cpu().numpy()[np.ix_(q, q)]
+    assert rel_rms(pruned, full) < 1e-6
+    M = torch.zeros((N2, N2), dtype=torch.complex64, device=DEV)
+    M[np.ix_(q, q)] = to_dev(S.random_image(n2, 12).astype(np.complex64), torch.complex64)
+    full = p.fft(M.clone(), "model").cpu().numpy()
+    pruned = p.fft(M.clone(), "model", pruned=True).cpu().numpy()
+    assert rel_rms(pruned, full) < 1e-6
+
+
 # ----------------------------------------------------------------------------------------
 # edge cases
 # ----------------------------------------------------------------------------------------
