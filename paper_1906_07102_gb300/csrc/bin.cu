@@ -186,24 +186,54 @@ __device__ __forceinline__ int dealt_position(int rho, int n) {
 __global__ void k_bin_scatter(const VisPos* __restrict__ pos, const int2* __restrict__ rank, long long nvis,
                               int W, int N, int n_strips, const int* __restrict__ offsets,
                               Rec* __restrict__ recs) {
-  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
-  for (long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; k < nvis; k += stride) {
-    const VisPos vp = pos[k];
-    if (vp.x0 < 0) continue;
-    const int2 rk = rank[k];
-    const int strip = vp.x0 / kStrip, xr = vp.x0 % kStrip;
-    const int odd = vp.y0 & 1;
-    // row pair (y0 & ~1, y0 | 1) of the strip: [offsets[g], offsets[g + 2])
-    const int* og = offsets + strip * N + (vp.y0 - odd);
-    int gs = og[0];
-    recs[gs + dealt_position((odd ? og[1] - gs : 0) + rk.x, og[2] - gs)] =
-        Rec{static_cast<unsigned>(k), rec_pack(vp.y0, xr), vp.su, vp.sv};
-    if (xr + W > kStrip) {
-      const int s2 = (strip + 1) % n_strips;
-      og = offsets + s2 * N + (vp.y0 - odd);
-      gs = og[0];
-      recs[gs + dealt_position((odd ? og[1] - gs : 0) + rk.y, og[2] - gs)] =
-          Rec{static_cast<unsigned>(k), rec_pack(vp.y0, xr - kStrip), vp.su, vp.sv};
+  // kCountIlp visibilities per thread per iteration: their position, rank and offset loads
+  // are in flight together (the pass is bound by the latency of these dependent loads)
+  const long long span = static_cast<long long>(blockDim.x) * kCountIlp;
+  const long long stride = static_cast<long long>(gridDim.x) * span;
+  for (long long base = static_cast<long long>(blockIdx.x) * span; base < nvis; base += stride) {
+    VisPos vp[kCountIlp];
+    int2 rk[kCountIlp];
+#pragma unroll
+    for (int u = 0; u < kCountIlp; ++u) {
+      const long long k = base + u * blockDim.x + threadIdx.x;
+      vp[u] = VisPos{-1, 0, 0u, 0u};
+      rk[u] = make_int2(0, 0);
+      if (k < nvis) {
+        vp[u] = pos[k];
+        rk[u] = rank[k];
+      }
+    }
+    int g1[kCountIlp], g2[kCountIlp];  // bucket pair bases (-1: none)
+#pragma unroll
+    for (int u = 0; u < kCountIlp; ++u) {
+      g1[u] = g2[u] = -1;
+      if (vp[u].x0 >= 0) {
+        const int strip = vp[u].x0 / kStrip, xr = vp[u].x0 % kStrip;
+        const int pair_row = vp[u].y0 & ~1;
+        g1[u] = strip * N + pair_row;
+        if (xr + W > kStrip) g2[u] = ((strip + 1) % n_strips) * N + pair_row;
+      }
+    }
+    int o1[kCountIlp][3], o2[kCountIlp][3];
+#pragma unroll
+    for (int u = 0; u < kCountIlp; ++u) {
+#pragma unroll
+      for (int e = 0; e < 3; ++e) {
+        o1[u][e] = g1[u] >= 0 ? offsets[g1[u] + e] : 0;
+        o2[u][e] = g2[u] >= 0 ? offsets[g2[u] + e] : 0;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kCountIlp; ++u) {
+      if (g1[u] < 0) continue;
+      const long long k = base + u * blockDim.x + threadIdx.x;
+      const int odd = vp[u].y0 & 1, xr = vp[u].x0 % kStrip;
+      // row pair (y0 & ~1, y0 | 1) of the strip: [offsets[g], offsets[g + 2])
+      recs[o1[u][0] + dealt_position((odd ? o1[u][1] - o1[u][0] : 0) + rk[u].x, o1[u][2] - o1[u][0])] =
+          Rec{static_cast<unsigned>(k), rec_pack(vp[u].y0, xr), vp[u].su, vp[u].sv};
+      if (g2[u] >= 0)
+        recs[o2[u][0] + dealt_position((odd ? o2[u][1] - o2[u][0] : 0) + rk[u].y, o2[u][2] - o2[u][0])] =
+            Rec{static_cast<unsigned>(k), rec_pack(vp[u].y0, xr - kStrip), vp[u].su, vp[u].sv};
     }
   }
 }
@@ -257,8 +287,6 @@ int bin_launch(const BinArgs& a, cudaStream_t st) {
   cudaMemsetAsync(a.hist, 0, sizeof(int) * L, st);
   cudaMemsetAsync(a.counters, 0, sizeof(int) * kNumCounters, st);
   const int threads = 256;
-  const long long want = (a.nvis + threads - 1) / threads;
-  const int blocks = static_cast<int>(want < a.max_blocks ? (want > 0 ? want : 1) : a.max_blocks);
   const long long want_c = (a.nvis + threads * kCountIlp - 1) / (threads * kCountIlp);
   const int blocks_c = static_cast<int>(want_c < a.max_blocks ? (want_c > 0 ? want_c : 1) : a.max_blocks);
   k_bin_count<<<blocks_c, threads, 0, st>>>(a.uv, a.nvis, a.scale2, a.W, a.N, a.n_strips, a.pos, a.rank, a.hist,
@@ -267,7 +295,7 @@ int bin_launch(const BinArgs& a, cudaStream_t st) {
   k_scan_partials<<<nchunks, kScanThreads, 0, st>>>(a.hist, L, a.partial);
   k_scan_top<<<1, 1024, 0, st>>>(a.partial, nchunks);
   k_scan_final<<<nchunks, kScanThreads, 0, st>>>(a.hist, L, a.partial, a.offsets);
-  k_bin_scatter<<<blocks, threads, 0, st>>>(a.pos, a.rank, a.nvis, a.W, a.N, a.n_strips, a.offsets, a.recs);
+  k_bin_scatter<<<blocks_c, threads, 0, st>>>(a.pos, a.rank, a.nvis, a.W, a.N, a.n_strips, a.offsets, a.recs);
   const int nblk = (a.N + a.rows_per_block - 1) / a.rows_per_block;
   const int ntask = a.n_strips * nblk;
   if (a.rows_per_block > kMaxRowsPerBlock) return -1;
