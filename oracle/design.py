@@ -197,6 +197,8 @@ def lm_table(h_half, W, x0p, Ms, Ng=NG_DEFAULT, Mg=MG_DEFAULT):
 # ---------------------------------------------------------------------------------------
 INTERP_NEAREST = 0
 INTERP_LINEAR = 1
+INTERP_QUADRATIC = 2
+INTERP_CUBIC = 3
 
 
 def nearest_row(s, Ms, decision_dtype=np.float64):
@@ -207,26 +209,55 @@ def nearest_row(s, Ms, decision_dtype=np.float64):
     return np.floor(t).astype(np.int64)
 
 
+def lagrange_stencil(t, Ms, d):
+    """First row k0 and local coordinate x = t - k0 of the degree-d stencil at t = s Ms:
+    rows k0 .. k0 + d with k0 = floor(t - (d - 1) / 2), the stencil centred on t and
+    clamped to the table's rows 0 .. Ms."""
+    k0 = np.clip(np.floor(t - 0.5 * (d - 1)).astype(np.int64), 0, Ms - d)
+    return k0, t - k0
+
+
+def lagrange_basis(x, d):
+    """L_m(x) = prod_{j != m} (x - j) / (m - j) on the nodes 0 .. d, shape (..., d + 1)."""
+    x = np.asarray(x, dtype=np.float64)
+    out = []
+    for m in range(d + 1):
+        v = np.ones_like(x)
+        for j in range(d + 1):
+            if j != m:
+                v = v * (x - j) / (m - j)
+        out.append(v)
+    return np.stack(out, axis=-1)
+
+
 def table_weights(T, Ms, s, interp, decision_dtype=np.float64):
-    """The W gridding weights for table coordinates s: nearest row, or linear
-    interpolation between rows k and k+1 with k = floor(s Ms) (Appendix F, d = 0, 1)."""
+    """The W gridding weights for table coordinates s (Appendix F, degree d = interp):
+    nearest row (d = 0); linear interpolation between rows k and k+1 with k = floor(s Ms)
+    (d = 1); Lagrange interpolation through the d + 1 rows of lagrange_stencil (d = 2, 3)."""
     s = np.asarray(s, dtype=np.float64)
     if interp == INTERP_NEAREST:
         return T[nearest_row(s, Ms, decision_dtype)]
     t = s * Ms
-    k = np.minimum(np.floor(t).astype(np.int64), Ms - 1)
-    f = (t - k)[:, None]
-    return (1.0 - f) * T[k] + f * T[k + 1]
+    if interp == INTERP_LINEAR:
+        k = np.minimum(np.floor(t).astype(np.int64), Ms - 1)
+        f = (t - k)[:, None]
+        return (1.0 - f) * T[k] + f * T[k + 1]
+    k0, x = lagrange_stencil(t, Ms, interp)
+    L = lagrange_basis(x, interp)
+    return sum(L[:, m, None] * T[k0 + m] for m in range(interp + 1))
 
 
 def _gauss_legendre_segments(Ms, interp, npts=8):
     """Nodes and weights on [0, 1) that integrate each smooth piece of the table function
-    separately (pieces of length 1/Ms; for nearest lookup they are centred on the rows)."""
+    separately (pieces of length 1/Ms; for nearest lookup they are centred on the rows;
+    for d = 2, 3 half-row pieces, which contain every stencil change)."""
     g, gw = np.polynomial.legendre.leggauss(npts)
     if interp == INTERP_LINEAR:
         edges = np.arange(Ms + 1, dtype=np.float64) / Ms
-    else:
+    elif interp == INTERP_NEAREST:
         edges = np.concatenate([[0.0], (np.arange(Ms, dtype=np.float64) + 0.5) / Ms, [1.0]])
+    else:
+        edges = np.arange(2 * Ms + 1, dtype=np.float64) / (2 * Ms)
     lo, hi = edges[:-1], edges[1:]
     half = 0.5 * (hi - lo)
     nodes = (0.5 * (hi + lo))[:, None] + half[:, None] * g[None, :]

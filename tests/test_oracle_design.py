@@ -181,21 +181,36 @@ def test_table_mirror_symmetry_and_size():
 
 
 def test_interpolation_error_order():
-    """Table error against the exact function falls as Ms^-1 (nearest) and Ms^-2
-    (linear) (Appendix F)."""
+    """Table error against the exact function falls as Ms^-(d+1) for interpolation of
+    degree d: Ms^-1 (nearest), Ms^-2 (linear), Ms^-3 (quadratic), Ms^-4 (cubic)
+    (Appendix F)."""
     W = 7
     h = h_opt(W)
     s = (np.arange(6000) + 0.37) / 6000
     exact = D.exact_C(h, W, X0P, s)
-    errs = {0: [], 1: []}
+    errs = {d: [] for d in range(4)}
     for Ms in (50, 100, 200):
         T = D.lm_table(h, W, X0P, Ms)
-        for interp in (0, 1):
-            errs[interp].append(np.abs(D.table_weights(T, Ms, s, interp) - exact).max())
-    p0 = np.log2(errs[0][0] / errs[0][2]) / 2
-    p1 = np.log2(errs[1][0] / errs[1][2]) / 2
-    assert abs(p0 - 1) < 0.15
-    assert abs(p1 - 2) < 0.15
+        for d in range(4):
+            errs[d].append(np.abs(D.table_weights(T, Ms, s, d) - exact).max())
+    for d in range(4):
+        p = np.log2(errs[d][0] / errs[d][2]) / 2
+        assert abs(p - (d + 1)) < 0.2, (d, p)
+    # at equal table size the higher degrees are far more accurate
+    assert errs[3][1] < 1e-3 * errs[1][1]
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_lagrange_interpolation_is_exact_on_polynomials(d):
+    """Rows sampled from a polynomial of degree d in s are reproduced exactly at any s,
+    including the clamped stencils at both ends of the table."""
+    Ms, W = 37, 3
+    rows = np.arange(Ms + 1) / Ms
+    coef = np.array([[0.3, -1.2, 0.7, 2.0][:d + 1], [1.0, 0.5, -0.25, 0.125][:d + 1], [-2.0, 0.0, 1.5, -0.5][:d + 1]])
+    poly = lambda s: np.stack([np.polyval(c[::-1], s) for c in coef], axis=-1)
+    T = poly(rows)
+    s = np.concatenate([np.linspace(0, 1, 1001), [0.0, 1.0, 0.5 / Ms, 1 - 0.5 / Ms]])
+    np.testing.assert_allclose(D.table_weights(T, Ms, s, d), poly(s), atol=1e-12)
 
 
 def test_optimal_correction_identities():
@@ -214,7 +229,7 @@ def test_optimal_correction_identities():
     assert np.max(np.abs(h[inside] * c[inside] - 1)) < 1e-6
 
 
-@pytest.mark.parametrize("interp", [0, 1])
+@pytest.mark.parametrize("interp", [0, 1, 2, 3])
 def test_correction_quadrature(interp):
     """Piecewise Gauss-Legendre (per table piece) against a dense midpoint rule."""
     W, Ms = 5, 40
