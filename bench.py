@@ -17,6 +17,10 @@ Two further workloads print their own line (not the headline):
                        (64 channels x 384 samples over 0.95-1.05 GHz), 4096^2 grid, W = 8:
                        forward + backward with all channels in one plan against one plan
                        per channel.
+  --workload large     high accuracy at scale: 128 antennas x 768 samples (8 h) x 32
+                       channels = 2.0e8 visibilities, 8192^2 grid, W = 12: float32 gridding
+                       with plain and with compensated (two-float) accumulation, errors
+                       against the float64 path and FP64-oracle spot checks.
 """
 import argparse
 import hashlib
@@ -46,7 +50,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="tracks", choices=["tracks", "channels", "autograd"])
+    ap.add_argument("--workload", default="tracks", choices=["tracks", "channels", "autograd", "large"])
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=0,
@@ -664,6 +668,103 @@ def run_autograd(args):
     print(json.dumps(line), flush=True)
 
 
+LARGE = dict(n_ant=128, hours=8.0, n_times=768, n_chan=32, f_lo=0.95e9, f_hi=1.05e9, N=8192, n_image=4096, x0=0.5,
+             W=12, oversample=1000, n_src=4, noise_sigma=0.1, crop=512, spot=100000)
+
+
+def run_large(args):
+    """Plain against compensated float32 accumulation at W = 12 on an 8192^2 grid."""
+    import torch
+    from oracle import design as D
+    from oracle import imaging as I
+    from paper_1906_07102_gb300 import lmg
+    from paper_1906_07102_gb300 import synthetic as S
+    torch.cuda.set_device(0)
+    a = LARGE
+    freqs = np.linspace(a["f_lo"], a["f_hi"], a["n_chan"])
+    uv = S.array_tracks(n_ant=a["n_ant"], hours=a["hours"], n_times=a["n_times"], freqs_hz=freqs, seed=0)
+    dl = S.pixel_scale_for(uv)
+    l, m, f = S.point_source_sky(a["n_src"], 0.45 * a["n_image"] * dl, seed=0)
+    vis = S.visibilities(uv, l, m, f, noise_sigma=a["noise_sigma"], seed=0)
+    model = S.gaussian_blob_image(a["n_image"], 64, seed=0).astype(np.complex128)
+    nv = uv.shape[0]
+    dev = torch.device("cuda", 0)
+    tab = lmg.Table(a["W"], a["x0"], a["oversample"], "linear")
+    uv_d = torch.from_numpy(uv).to(dev)
+    v64 = torch.from_numpy(vis.astype(np.complex64)).to(dev)
+    m64 = torch.from_numpy(model.astype(np.complex64)).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    p32 = lmg.Plan(tab, a["n_image"], dl, nv, "c64")
+    p32.bin(uv_d)
+    grid = torch.empty((a["N"], a["N"]), dtype=torch.complex64, device=dev)
+    out = torch.empty_like(v64)
+    for _ in range(max(2, args.warmup)):
+        p32.grid(v64, out=grid)
+        p32.grid(v64, accum="compensated", out=grid)
+        p32.degrid(grid, out=out)
+    torch.cuda.synchronize()
+    steps = max(3, min(args.steps, 10))
+    clocks = Clocks(0)
+    clocks.start()
+    ms_plain = _events_ms(lambda: p32.grid(v64, out=grid), steps, flush, stream, torch)
+    ms_comp = _events_ms(lambda: p32.grid(v64, accum="compensated", out=grid), steps, flush, stream, torch)
+    ms_degrid = _events_ms(lambda: p32.degrid(grid, out=out), steps, flush, stream, torch)
+    clk = clocks.stop()
+    c = a["crop"]
+    sl = slice(a["n_image"] // 2 - c // 2, a["n_image"] // 2 + c // 2)
+    img_plain = p32.dirty_image(v64)[sl, sl].cpu().numpy()
+    img_comp = p32.dirty_image(v64, accum="compensated")[sl, sl].cpu().numpy()
+    pv32 = p32.predict_vis(m64).cpu().numpy()
+    del p32, grid, out
+    torch.cuda.empty_cache()
+    # float64 path of the library (kernel parity with the oracle: 1e-12 on shared tables)
+    p64 = lmg.Plan(tab, a["n_image"], dl, nv, "c128")
+    p64.bin(uv_d)
+    img64 = p64.dirty_image(torch.from_numpy(vis).to(dev))[sl, sl].cpu().numpy()
+    pv64 = p64.predict_vis(torch.from_numpy(model).to(dev)).cpu().numpy()
+    del p64
+    torch.cuda.empty_cache()
+
+    def rel(x, ref):
+        return float(np.sqrt(np.mean(np.abs(x - ref) ** 2) / np.mean(np.abs(ref) ** 2)))
+
+    # FP64 oracle spot check: predicted visibilities at sampled positions
+    k = np.sort(np.random.default_rng(5).choice(nv, a["spot"], replace=False))
+    T = D.lm_table(D.least_misfit_h(a["W"], a["x0"] / 2), a["W"], a["x0"] / 2, a["oversample"])
+    hv = D.correction_factors(T, a["oversample"], 1, a["W"], I.pixel_coords(a["n_image"], a["N"]))
+    uc = I.cells_from_wavelengths(uv[k], a["N"], dl)
+    op = I.Plan(uc[:, 0], uc[:, 1], a["W"], a["N"], single_precision_s=False)
+    ref_pv = I.degrid(op, T, a["oversample"], 1, I.model_grid(I.pad_correct(model, hv, a["N"])))
+    algo = nv * 48 + 2 * a["N"] ** 2 * 8
+    peak, src = measured_peak_hbm()
+    ms = ms_plain + ms_degrid
+    line = {"metric": "Mvis/s grid+degrid at W=12, 8192^2 grid (float32 plain vs compensated accumulation); "
+                      "relative RMS error vs FP64",
+            "value": nv / (ms * 1e-3) / 1e6, "unit": "Mvis/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "128-antenna 8 h tracks, 768 samples x 32 channels (0.95-1.05 GHz), "
+                                   f"{nv} vis, 4 point sources + noise, 8192^2 grid, 4096^2 image, W=12 (QR table), "
+                                   "linear table M_s=1000, complex64", "nvis": nv, "parallelism": "single GPU",
+                       "l2": "flushed before every timed pass (256 MB write, outside the events)"},
+            "stages_ms": {"grid_plain": ms_plain, "grid_compensated": ms_comp, "degrid": ms_degrid},
+            "compensated_grid_degrid_mvis_s": nv / ((ms_comp + ms_degrid) * 1e-3) / 1e6,
+            "accuracy": {
+                "dirty_image_plain_vs_fp64_path": rel(img_plain, img64),
+                "dirty_image_compensated_vs_fp64_path": rel(img_comp, img64),
+                "predicted_vis_vs_fp64_path": rel(pv32, pv64),
+                "predicted_vis_vs_fp64_oracle": rel(pv32[k], ref_pv),
+                "fp64_path_predicted_vis_vs_fp64_oracle": rel(pv64[k], ref_pv),
+                "sample": f"central {c}^2 of the 4096^2 dirty image against the library's float64 path; "
+                          f"{a['spot']} predicted visibilities against the FP64 oracle (full 8192^2 model grid)"},
+            "roofline": {"kernel": "grid (plain) + degrid passes", "bound": "hbm", "achieved": algo / (ms * 1e-3) / 1e9,
+                         "peak": peak, "unit": "GB/s", "frac": algo / (ms * 1e-3) / 1e9 / peak, "traffic": None,
+                         "algorithmic_bytes": algo, "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)"},
+            "clocks": clk, "gpu_launches": 4 * steps}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -672,6 +773,8 @@ def main():
         run_channels(args)
     elif args.workload == "autograd":
         run_autograd(args)
+    elif args.workload == "large":
+        run_large(args)
     else:
         run_native(args)
 

@@ -61,7 +61,7 @@ typedef enum {
 } lmg_status;
 
 enum { LMG_C64 = 0, LMG_C128 = 1 };
-enum { LMG_INTERP_NEAREST = 0, LMG_INTERP_LINEAR = 1 };
+enum { LMG_INTERP_NEAREST = 0, LMG_INTERP_LINEAR = 1, LMG_INTERP_QUADRATIC = 2, LMG_INTERP_CUBIC = 3 };
 enum { LMG_CORR_HOPT = 0, LMG_CORR_INV_C = 1 };
 enum { LMG_ACCUM_PLAIN = 0, LMG_ACCUM_COMPENSATED = 1 };
 enum { LMG_CROP = 0, LMG_PAD = 1 };
@@ -85,7 +85,13 @@ typedef struct lmg_batch lmg_batch; /* many independent channels gridded togethe
  *   W          support width, 1..16
  *   x0         kept fraction of the FFT image, 0 < x0 <= 1 (paper's x0 = x0 / 2)
  *   oversample table sampling rate M_s per cell, 2..1000000
- *   interp     LMG_INTERP_NEAREST or LMG_INTERP_LINEAR (Appendix F, d = 0 or 1)
+ *   interp     table interpolation of degree d (Appendix F): LMG_INTERP_NEAREST (d = 0),
+ *              LMG_INTERP_LINEAR (d = 1), LMG_INTERP_QUADRATIC (d = 2) or LMG_INTERP_CUBIC
+ *              (d = 3). For d >= 2, t = s * oversample is interpolated through rows
+ *              k0 .. k0 + d, k0 = floor(t - (d - 1) / 2) clamped to [0, oversample - d],
+ *              with the Lagrange basis on those rows; the table error falls as
+ *              oversample^-(d+1), so d = 3 reaches linear's accuracy with a far smaller
+ *              table (oversample >= d required)
  *   correction LMG_CORR_HOPT (h = c / D, Eqs. 12, 15) or LMG_CORR_INV_C (h = 1/c)
  *   out        receives the new table (caller frees with lmg_table_free)
  * Returns LMG_EINVAL on a bad argument, LMG_ENOMEM, LMG_ENOCONV if the optimiser fails.

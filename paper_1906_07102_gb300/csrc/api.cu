@@ -39,8 +39,9 @@ bool check_table_args(int W, double x0, int Ms, int interp, int correction) {
   if (W < 1 || W > kMaxW) return set_error(LMG_EINVAL, "W must be in [1, 16]"), false;
   if (!(x0 > 0.0 && x0 <= 1.0)) return set_error(LMG_EINVAL, "x0 must be in (0, 1]"), false;
   if (Ms < 2 || Ms > 1000000) return set_error(LMG_EINVAL, "oversample must be in [2, 1000000]"), false;
-  if (interp != LMG_INTERP_NEAREST && interp != LMG_INTERP_LINEAR)
-    return set_error(LMG_EINVAL, "interp must be LMG_INTERP_NEAREST or LMG_INTERP_LINEAR"), false;
+  if (interp < LMG_INTERP_NEAREST || interp > LMG_INTERP_CUBIC)
+    return set_error(LMG_EINVAL, "interp must be LMG_INTERP_NEAREST, _LINEAR, _QUADRATIC or _CUBIC"), false;
+  if (Ms < interp) return set_error(LMG_EINVAL, "oversample must be at least the interpolation degree"), false;
   if (correction != LMG_CORR_HOPT && correction != LMG_CORR_INV_C)
     return set_error(LMG_EINVAL, "correction must be LMG_CORR_HOPT or LMG_CORR_INV_C"), false;
   return true;

@@ -88,20 +88,40 @@ template <int W, typename R> struct Stage {
 template <typename R>
 __device__ __forceinline__ void table_coord(int Wp, int Ms, int interp, unsigned S, int& off, R& f) {
   const unsigned long long Pm = static_cast<unsigned long long>(S) * static_cast<unsigned>(Ms);
-  if (interp) {
+  if (interp == 1) {
     off = static_cast<int>(Pm >> 32) * Wp;
     f = static_cast<R>(static_cast<unsigned>(Pm & 0xffffffffull)) * static_cast<R>(2.3283064365386962890625e-10);
-  } else {
+  } else if (interp == 0) {
     off = static_cast<int>((Pm + 0x80000000ull) >> 32) * Wp;
     f = R(0);
+  } else {
+    // degree d = interp: first stencil row k0 = floor(t - (d - 1) / 2), clamped to
+    // [0, Ms - d], and f = t - k0 in [0, d] (t = S Ms 2^-32)
+    const long long P = static_cast<long long>(Pm);
+    long long k0 = (P - static_cast<long long>(interp - 1) * 0x80000000ll) >> 32;
+    k0 = k0 < 0 ? 0 : (k0 > Ms - interp ? Ms - interp : k0);
+    off = static_cast<int>(k0) * Wp;
+    f = static_cast<R>(P - (k0 << 32)) * static_cast<R>(2.3283064365386962890625e-10);
   }
+}
+
+// Lagrange interpolation of degree d (2 or 3) through the rows p[0], p[Wp], ..., p[d Wp]
+// at local coordinate x in [0, d] (Appendix F for d > 1).
+template <typename R>
+__device__ __forceinline__ R lagrange_entry(const R* __restrict__ p, int Wp, int d, R x) {
+  const R a = x, b = x - R(1), c = x - R(2);
+  if (d == 2) return R(0.5) * b * c * p[0] - a * c * p[Wp] + R(0.5) * a * b * p[2 * Wp];
+  const R e = x - R(3), sixth = R(1) / R(6);
+  return -sixth * b * c * e * p[0] + R(0.5) * a * c * e * p[Wp] - R(0.5) * a * b * e * p[2 * Wp] +
+         sixth * a * b * c * p[3 * Wp];
 }
 
 // Stages the weights of a chunk's records, held one per lane by lanes lo .. hi-1 (table
 // row offsets and fractions for u and v, row offset d in the group, and for gridding
 // w V): Cv shifted by d into s_cv (entry q of record l at q * pitch + l, zero for q
 // outside [d, d + W)) and Cu, times w V when gridding, into s_u[l * W + i]. G lanes share
-// a record and compute one table entry each (C = T[k] + f (T[k+1] - T[k])), so a round's
+// a record and compute one table entry each (C = T[k] + f (T[k+1] - T[k]), or Lagrange
+// through d + 1 rows), so a round's
 // table reads touch P rows instead of 32 rows per instruction.
 template <int W, typename R, bool GRID>
 __device__ __forceinline__ void stage_chunk(const R* __restrict__ tab, int Wp, int interp, int lo, int hi, int ou,
@@ -125,10 +145,17 @@ __device__ __forceinline__ void stage_chunk(const R* __restrict__ tab, int Wp, i
     }
     if (r < hi) {
       if (i < W) {
-        R cu = tab[ou_r + i], cv = tab[ov_r + i];
-        if (interp) {
-          cu = cu + fu_r * (tab[ou_r + Wp + i] - cu);
-          cv = cv + fv_r * (tab[ov_r + Wp + i] - cv);
+        R cu, cv;
+        if (interp <= 1) {
+          cu = tab[ou_r + i];
+          cv = tab[ov_r + i];
+          if (interp) {
+            cu = cu + fu_r * (tab[ou_r + Wp + i] - cu);
+            cv = cv + fv_r * (tab[ov_r + Wp + i] - cv);
+          }
+        } else {
+          cu = lagrange_entry<R>(tab + ou_r + i, Wp, interp, fu_r);
+          cv = lagrange_entry<R>(tab + ov_r + i, Wp, interp, fv_r);
         }
         if constexpr (GRID) {
           C2 t;

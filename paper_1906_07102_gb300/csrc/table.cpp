@@ -400,10 +400,12 @@ void correction_factors(const lmg_table* t, int64_t n_image, int64_t N, bool sin
   if (Ms <= 4096) {
     if (t->interp == LMG_INTERP_LINEAR) {
       for (int k = 0; k <= Ms; ++k) edges.push_back(double(k) / Ms);
-    } else {
+    } else if (t->interp == LMG_INTERP_NEAREST) {
       edges.push_back(0.0);
       for (int k = 0; k < Ms; ++k) edges.push_back((k + 0.5) / Ms);
       edges.push_back(1.0);
+    } else {  // degree 2, 3: half-row pieces contain every change of stencil
+      for (int k = 0; k <= 2 * Ms; ++k) edges.push_back(double(k) / (2.0 * Ms));
     }
   } else {
     for (int k = 0; k <= 4096; ++k) edges.push_back(double(k) / 4096);
@@ -423,6 +425,25 @@ void correction_factors(const lmg_table* t, int64_t n_image, int64_t N, bool sin
         double f = tt - k;
         for (int j = 0; j < W; ++j)
           Cn[q * W + j] = (1.0 - f) * T[size_t(k) * W + j] + f * T[size_t(k + 1) * W + j];
+      } else if (t->interp >= LMG_INTERP_QUADRATIC) {
+        // Lagrange interpolation of degree d through rows k0 .. k0 + d (Appendix F)
+        const int d = t->interp;
+        const double tt = s * Ms;
+        int k0 = int(std::floor(tt - 0.5 * (d - 1)));
+        k0 = std::max(0, std::min(k0, Ms - d));
+        const double x = tt - k0;
+        double L[4];
+        for (int m = 0; m <= d; ++m) {
+          double v = 1.0;
+          for (int jj = 0; jj <= d; ++jj)
+            if (jj != m) v *= (x - jj) / double(m - jj);
+          L[m] = v;
+        }
+        for (int j = 0; j < W; ++j) {
+          double v = 0.0;
+          for (int m = 0; m <= d; ++m) v += L[m] * T[size_t(k0 + m) * W + j];
+          Cn[q * W + j] = v;
+        }
       } else {
         int k = int(std::floor(s * Ms + 0.5));
         for (int j = 0; j < W; ++j) Cn[q * W + j] = T[size_t(k) * W + j];

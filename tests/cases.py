@@ -12,7 +12,7 @@ from oracle import design as D
 from oracle import imaging as I
 from paper_1906_07102_gb300 import synthetic as S
 
-INTERP = {"nearest": 0, "linear": 1}
+INTERP = {"nearest": 0, "linear": 1, "quadratic": 2, "cubic": 3}
 
 
 @functools.lru_cache(maxsize=None)

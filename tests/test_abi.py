@@ -43,7 +43,8 @@ def test_every_declared_function_is_exported_and_bound(lmg):
 @pytest.mark.parametrize("args,msg", [
     ((0, 0.5, 100, 1, 0), "W must be"), ((17, 0.5, 100, 1, 0), "W must be"),
     ((7, 0.0, 100, 1, 0), "x0 must be"), ((7, 1.5, 100, 1, 0), "x0 must be"),
-    ((7, 0.5, 1, 1, 0), "oversample"), ((7, 0.5, 100, 2, 0), "interp"), ((7, 0.5, 100, 1, 5), "correction")])
+    ((7, 0.5, 1, 1, 0), "oversample"), ((7, 0.5, 100, 4, 0), "interp"), ((7, 0.5, 100, -1, 0), "interp"),
+    ((7, 0.5, 2, 3, 0), "at least the interpolation degree"), ((7, 0.5, 100, 1, 5), "correction")])
 def test_table_argument_errors(lmg, args, msg):
     h = ctypes.c_void_p()
     rc = lmg.lib().lmg_kernel_table(*args, ctypes.byref(h))
@@ -59,7 +60,7 @@ def test_null_outputs_are_rejected(lmg):
     assert L.lmg_grid(None, None, None, 0, None, None) == -1
 
 
-@pytest.mark.parametrize("W,Ms,interp", [(3, 100, "nearest"), (5, 200, "linear")])
+@pytest.mark.parametrize("W,Ms,interp", [(3, 100, "nearest"), (5, 200, "linear"), (5, 60, "cubic")])
 def test_library_table_matches_oracle(lmg, W, Ms, interp):
     """The library's C++ optimiser and the oracle's scipy one reach the same optimum; the
     optimum of E is determined to about 1e-9 in float64 (flat directions of h)."""
@@ -73,7 +74,7 @@ def test_library_table_matches_oracle(lmg, W, Ms, interp):
     assert np.abs(h - ho).max() <= 1e-5
     n_img, N = 64, 128
     hv = t.correction(n_img)
-    hvo = D.correction_factors(Co, Ms, 1 if interp == "linear" else 0, W, I.pixel_coords(n_img, N))
+    hvo = D.correction_factors(Co, Ms, {"nearest": 0, "linear": 1, "cubic": 3}[interp], W, I.pixel_coords(n_img, N))
     np.testing.assert_allclose(hv, hvo, rtol=1e-6)
 
 

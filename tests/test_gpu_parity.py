@@ -18,7 +18,7 @@ from oracle import design as D  # noqa: E402
 from oracle import imaging as I  # noqa: E402
 from paper_1906_07102_gb300 import lmg  # noqa: E402
 from paper_1906_07102_gb300 import synthetic as S  # noqa: E402
-from tests.cases import (caller_table, disk_case, oracle_hvec, oracle_table, rel_rms,  # noqa: E402
+from tests.cases import (INTERP, caller_table, disk_case, oracle_hvec, oracle_table, rel_rms,  # noqa: E402
                          track_case)
 
 pytestmark = pytest.mark.gpu
@@ -205,6 +205,26 @@ def test_pruned_ffts_match_full_fft_on_the_kept_field(c2):
     assert rel_rms(pruned, full) < 1e-6
 
 
+@pytest.mark.parametrize("interp,Ms", [("quadratic", 200), ("cubic", 100)])
+def test_fp32_higher_degree_tables(c2, interp, Ms):
+    """Quadratic and cubic table interpolation (Appendix F) through the float32 path: dirty
+    image and prediction against the oracle with the same degree, table size and own
+    least-misfit table, at the float32 target; the correction factors of both sides use
+    the same interpolated function."""
+    uv, dl, vis, p2, T2, hv2, op = c2
+    p = gpu_plan(W2, 0.5, Ms, interp, n2, dl, uv.shape[0], "c64")
+    p.bin(to_dev(uv, torch.float64))
+    T = oracle_table(W2, 0.5, Ms)
+    hv = oracle_hvec(T, Ms, interp, W2, n2, N2)
+    img = p.dirty_image(to_dev(vis, torch.complex64)).cpu().numpy()
+    ref = I.dirty_image(op, T, Ms, INTERP[interp], hv, n2, vis.astype(np.complex128))
+    assert rel_rms(img, ref) < 1e-5
+    model = S.gaussian_blob_image(n2, 32, seed=13).astype(np.complex64)
+    pv = p.predict_vis(to_dev(model, torch.complex64)).cpu().numpy()
+    pref = I.predict_vis(op, T, Ms, INTERP[interp], hv, model.astype(np.complex128))
+    assert rel_rms(pv, pref) < 1e-5
+
+
 # ----------------------------------------------------------------------------------------
 # edge cases
 # ----------------------------------------------------------------------------------------
@@ -214,17 +234,17 @@ def test_support_widths_fp64_kernel_exact(W):
     uv, dl = disk_case(nvis, N, seed=W)
     vis = S.complex_normal(nvis, W)
     T = caller_table(W, Ms)
-    for interp in ("nearest", "linear"):
+    for interp in ("nearest", "linear", "quadratic", "cubic"):
         p = gpu_plan(W, 0.5, Ms, interp, n_img, dl, nvis, "c128", values=T)
         p.bin(to_dev(uv, torch.float64))
         g = p.grid(to_dev(vis, torch.complex128)).cpu().numpy()
         op = oracle_plan(uv, dl, W, N, single=False)
-        ref = I.grid(op, T, Ms, 1 if interp == "linear" else 0, vis)
-        assert np.abs(g - ref).max() <= 1e-12 * np.abs(ref).max()
+        ref = I.grid(op, T, Ms, INTERP[interp], vis)
+        assert np.abs(g - ref).max() <= 1e-12 * np.abs(ref).max(), interp
         Gm = S.random_image(N, W + 1)
         vd = p.degrid(to_dev(Gm, torch.complex128)).cpu().numpy()
-        vref = I.degrid(op, T, Ms, 1 if interp == "linear" else 0, Gm)
-        assert np.abs(vd - vref).max() <= 1e-12 * np.abs(vref).max()
+        vref = I.degrid(op, T, Ms, INTERP[interp], Gm)
+        assert np.abs(vd - vref).max() <= 1e-12 * np.abs(vref).max(), interp
 
 
 @pytest.mark.parametrize("nvis", [0, 1, 31, 33, 4097])
