@@ -61,7 +61,8 @@ typedef enum {
 } lmg_status;
 
 enum { LMG_C64 = 0, LMG_C128 = 1 };
-enum { LMG_INTERP_NEAREST = 0, LMG_INTERP_LINEAR = 1, LMG_INTERP_QUADRATIC = 2, LMG_INTERP_CUBIC = 3 };
+enum { LMG_INTERP_NEAREST = 0, LMG_INTERP_LINEAR = 1, LMG_INTERP_QUADRATIC = 2, LMG_INTERP_CUBIC = 3,
+       LMG_INTERP_DIRECT = 4 };
 enum { LMG_CORR_HOPT = 0, LMG_CORR_INV_C = 1 };
 enum { LMG_ACCUM_PLAIN = 0, LMG_ACCUM_COMPENSATED = 1 };
 enum { LMG_CROP = 0, LMG_PAD = 1 };
@@ -91,7 +92,13 @@ typedef struct lmg_batch lmg_batch; /* many independent channels gridded togethe
  *              k0 .. k0 + d, k0 = floor(t - (d - 1) / 2) clamped to [0, oversample - d],
  *              with the Lagrange basis on those rows; the table error falls as
  *              oversample^-(d+1), so d = 3 reaches linear's accuracy with a far smaller
- *              table (oversample >= d required)
+ *              table (oversample >= d required). LMG_INTERP_DIRECT: no table lookup;
+ *              the gridding weights of every visibility are calculated directly from the
+ *              normal equations, C(s) = A^-1 B(s) (Section 5.2, Eqs. 17-19), with A^-1 and
+ *              the node sums folded into W x 33 cosine and sine coefficients on the host;
+ *              exact function values at a higher cost. float64 plans and W <= 11 only (the
+ *              normal equations' range, Appendix B); tables from lmg_table_from_values
+ *              cannot use it (they carry no h)
  *   correction LMG_CORR_HOPT (h = c / D, Eqs. 12, 15) or LMG_CORR_INV_C (h = 1/c)
  *   out        receives the new table (caller frees with lmg_table_free)
  * Returns LMG_EINVAL on a bad argument, LMG_ENOMEM, LMG_ENOCONV if the optimiser fails.

@@ -275,11 +275,16 @@ def correction_factors(T, Ms, interp, W, x, mode=CORRECTION_HOPT, npts=8):
     c(x) = int_0^1 ds sum_j C_j(s) cos(2 pi d_j(s) x)               (Eq. 13)
     D(x) = int_0^1 ds |sum_j C_j(s) exp(i 2 pi d_j(s) x)|^2         (Eqs. 12, 14)
     h_opt = c / D (Eqs. 12, 15); the alternative mode returns 1/c (Section 3).
-    The s-integral uses 8-point Gauss-Legendre per table piece.
+    The s-integral uses 8-point Gauss-Legendre per table piece. When T is a function of s
+    (direct calculation, Section 5.2: the exact, smooth C) it uses 64 equal pieces.
     """
     x = np.asarray(x, dtype=np.float64)
-    sn, sw = _gauss_legendre_segments(Ms, interp, npts)
-    Cn = table_weights(T, Ms, sn, interp)                  # (S, W)
+    if callable(T):
+        sn, sw = _gauss_legendre_segments(64, INTERP_LINEAR, npts)
+        Cn = T(sn)
+    else:
+        sn, sw = _gauss_legendre_segments(Ms, interp, npts)
+        Cn = table_weights(T, Ms, sn, interp)              # (S, W)
     d = support_offsets(sn, W)                             # (S, W)
     c = np.empty(x.size)
     D = np.empty(x.size)

@@ -76,10 +76,14 @@ class Plan:
         self.single = single_precision_s
 
     def weights(self, T, Ms, interp):
-        """Per-axis weights Cu (K, W) and Cv (K, W) from the table (Section 5.1, App. F)."""
-        dd = np.float32 if self.single else np.float64
-        Cu = D.table_weights(T, Ms, self.su, interp, dd)
-        Cv = D.table_weights(T, Ms, self.sv, interp, dd)
+        """Per-axis weights Cu (K, W) and Cv (K, W) from the table (Section 5.1, App. F), or,
+        when T is a function of s (direct calculation, Section 5.2), T(s) itself."""
+        if callable(T):
+            Cu, Cv = T(self.su), T(self.sv)
+        else:
+            dd = np.float32 if self.single else np.float64
+            Cu = D.table_weights(T, Ms, self.su, interp, dd)
+            Cv = D.table_weights(T, Ms, self.sv, interp, dd)
         Cu[~self.valid] = 0.0
         Cv[~self.valid] = 0.0
         return Cu, Cv

@@ -39,9 +39,10 @@ bool check_table_args(int W, double x0, int Ms, int interp, int correction) {
   if (W < 1 || W > kMaxW) return set_error(LMG_EINVAL, "W must be in [1, 16]"), false;
   if (!(x0 > 0.0 && x0 <= 1.0)) return set_error(LMG_EINVAL, "x0 must be in (0, 1]"), false;
   if (Ms < 2 || Ms > 1000000) return set_error(LMG_EINVAL, "oversample must be in [2, 1000000]"), false;
-  if (interp < LMG_INTERP_NEAREST || interp > LMG_INTERP_CUBIC)
-    return set_error(LMG_EINVAL, "interp must be LMG_INTERP_NEAREST, _LINEAR, _QUADRATIC or _CUBIC"), false;
-  if (Ms < interp) return set_error(LMG_EINVAL, "oversample must be at least the interpolation degree"), false;
+  if (interp < LMG_INTERP_NEAREST || interp > LMG_INTERP_DIRECT)
+    return set_error(LMG_EINVAL, "interp must be LMG_INTERP_NEAREST, _LINEAR, _QUADRATIC, _CUBIC or _DIRECT"), false;
+  if (interp <= LMG_INTERP_CUBIC && Ms < interp)
+    return set_error(LMG_EINVAL, "oversample must be at least the interpolation degree"), false;
   if (correction != LMG_CORR_HOPT && correction != LMG_CORR_INV_C)
     return set_error(LMG_EINVAL, "correction must be LMG_CORR_HOPT or LMG_CORR_INV_C"), false;
   return true;
@@ -244,13 +245,30 @@ int plan_create(const lmg_table* t, int64_t n_image, double pixel_scale, int64_t
   // Device table (rows padded to Wp) and correction factors in the plan's precision.
   std::vector<double> hcorr(static_cast<size_t>(n_image));
   correction_factors(t, n_image, N, dtype == LMG_C64, hcorr.data());
-  std::vector<unsigned char> tab_bytes(size_t(p->Ms + 1) * p->Wp * rs, 0), h_bytes(size_t(n_image) * rs);
-  for (int i = 0; i <= p->Ms; ++i)
-    for (int j = 0; j < p->W; ++j) {
-      const double v = t->C[size_t(i) * p->W + j];
-      if (rs == 8) reinterpret_cast<double*>(tab_bytes.data())[size_t(i) * p->Wp + j] = v;
-      else reinterpret_cast<float*>(tab_bytes.data())[size_t(i) * p->Wp + j] = float(v);
+  std::vector<unsigned char> tab_bytes, h_bytes(size_t(n_image) * rs);
+  if (t->interp == LMG_INTERP_DIRECT) {
+    // direct calculation: the coefficient block takes the place of the table rows
+    if (dtype != LMG_C128) {
+      delete p;
+      return set_error(LMG_EUNSUPPORTED, "LMG_INTERP_DIRECT runs on float64 plans (LMG_C128)");
     }
+    std::vector<double> coef;
+    if ((rc = direct_coefficients(t, coef)) != LMG_OK) {
+      delete p;
+      return rc;
+    }
+    p->Ms = int((coef.size() + size_t(p->Wp) - 1) / size_t(p->Wp)) - 1;
+    tab_bytes.assign(size_t(p->Ms + 1) * p->Wp * rs, 0);
+    std::memcpy(tab_bytes.data(), coef.data(), coef.size() * sizeof(double));
+  } else {
+    tab_bytes.assign(size_t(p->Ms + 1) * p->Wp * rs, 0);
+    for (int i = 0; i <= p->Ms; ++i)
+      for (int j = 0; j < p->W; ++j) {
+        const double v = t->C[size_t(i) * p->W + j];
+        if (rs == 8) reinterpret_cast<double*>(tab_bytes.data())[size_t(i) * p->Wp + j] = v;
+        else reinterpret_cast<float*>(tab_bytes.data())[size_t(i) * p->Wp + j] = float(v);
+      }
+  }
   for (int64_t q = 0; q < n_image; ++q) {
     if (rs == 8) reinterpret_cast<double*>(h_bytes.data())[q] = hcorr[size_t(q)];
     else reinterpret_cast<float*>(h_bytes.data())[q] = float(hcorr[size_t(q)]);
@@ -394,6 +412,8 @@ int lmg_table_from_values(int W, double x0, int oversample, int interp, int corr
   *out = nullptr;
   if (!C_host) return set_error(LMG_EINVAL, "C_host is NULL");
   if (!check_table_args(W, x0, oversample, interp, correction)) return LMG_EINVAL;
+  if (interp == LMG_INTERP_DIRECT)
+    return set_error(LMG_EINVAL, "LMG_INTERP_DIRECT needs a least-misfit table from lmg_kernel_table");
   lmg_table* t = new (std::nothrow) lmg_table;
   if (!t) return set_error(LMG_ENOMEM, "host allocation failed");
   t->W = W;

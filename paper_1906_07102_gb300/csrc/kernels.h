@@ -6,6 +6,9 @@
 
 namespace lmg {
 
+// Nodes k = 0..Ng of the direct calculation's folded sums (Ng = 32, Appendix A).
+constexpr int kDirectNodes = 33;
+
 struct VisPos;
 struct Rec;
 struct Item;

@@ -45,6 +45,11 @@ int build_least_misfit(int W, double x0p, int Ms, lmg_table* t);
 // float32-rounded) table function; table.cpp.
 void correction_factors(const lmg_table* t, int64_t n_image, int64_t N, bool single_precision,
                         double* h_out);
+// Coefficients of the direct calculation (LMG_INTERP_DIRECT), table.cpp: out[0] = phi =
+// 2 pi x0 / Ng, out[1 + a (Ng+1) + k] = alpha[a][k], out[1 + (W + a)(Ng+1) + k] = beta[a][k]
+// with C_a(s) = sum_k alpha[a][k] cos(k phi s) + beta[a][k] sin(k phi s).
+int direct_coefficients(const lmg_table* t, std::vector<double>& out);
+constexpr int kDirectMaxW = 11;
 
 }  // namespace lmg
 

@@ -94,6 +94,8 @@ extern "C" int lmg_grid_static(const lmg_table* t, int64_t n_image, double pixel
   if (nvis > 0 && (!uv || !vis)) return set_error(LMG_EINVAL, "uv or vis is NULL");
   if (reinterpret_cast<uintptr_t>(uv) % 16 != 0) return set_error(LMG_EINVAL, "uv must be 16-byte aligned");
   if (!(pixel_scale > 0.0) || !std::isfinite(pixel_scale)) return set_error(LMG_EINVAL, "pixel_scale must be > 0");
+  if (t->interp == LMG_INTERP_DIRECT)
+    return set_error(LMG_EUNSUPPORTED, "lmg_grid_static runs float32 tables; LMG_INTERP_DIRECT needs a float64 plan");
   if (t->Ms > kMaxOversample)
     return set_error(LMG_EINVAL, "table oversample must be at most " + std::to_string(kMaxOversample) +
                                      " for lmg_grid_static");

@@ -94,6 +94,10 @@ __device__ __forceinline__ void table_coord(int Wp, int Ms, int interp, unsigned
   } else if (interp == 0) {
     off = static_cast<int>((Pm + 0x80000000ull) >> 32) * Wp;
     f = R(0);
+  } else if (interp == 4) {
+    // direct calculation: the coefficients replace the rows; f = s
+    off = 0;
+    f = static_cast<R>(S) * static_cast<R>(2.3283064365386962890625e-10);
   } else {
     // degree d = interp: first stencil row k0 = floor(t - (d - 1) / 2), clamped to
     // [0, Ms - d], and f = t - k0 in [0, d] (t = S Ms 2^-32)
@@ -103,6 +107,26 @@ __device__ __forceinline__ void table_coord(int Wp, int Ms, int interp, unsigned
     off = static_cast<int>(k0) * Wp;
     f = static_cast<R>(P - (k0 << 32)) * static_cast<R>(2.3283064365386962890625e-10);
   }
+}
+
+// Direct calculation (Section 5.2, float64 plans): C_a(s) = sum_k alpha[a][k] cos(k phi s) +
+// beta[a][k] sin(k phi s), coef = {phi, alpha[W][33], beta[W][33]} (A^-1 and the node sums
+// folded in on the host); cos/sin(k phi s) by rotation from one sincos.
+template <typename R>
+__device__ __forceinline__ R direct_entry(const R* __restrict__ coef, int W, int a, R s) {
+  R sn, cs;
+  if constexpr (sizeof(R) == 8) sincos(coef[0] * s, &sn, &cs);
+  else sincosf(coef[0] * s, &sn, &cs);
+  const R* al = coef + 1 + a * kDirectNodes;
+  const R* be = coef + 1 + (W + a) * kDirectNodes;
+  R ck = R(1), sk = R(0), acc = al[0];
+  for (int k = 1; k < kDirectNodes; ++k) {
+    const R c2 = ck * cs - sk * sn;
+    sk = ck * sn + sk * cs;
+    ck = c2;
+    acc += al[k] * ck + be[k] * sk;
+  }
+  return acc;
 }
 
 // Lagrange interpolation of degree d (2 or 3) through the rows p[0], p[Wp], ..., p[d Wp]
@@ -153,6 +177,9 @@ __device__ __forceinline__ void stage_chunk(const R* __restrict__ tab, int Wp, i
             cu = cu + fu_r * (tab[ou_r + Wp + i] - cu);
             cv = cv + fv_r * (tab[ov_r + Wp + i] - cv);
           }
+        } else if (interp == 4) {
+          cu = direct_entry<R>(tab, W, i, fu_r);
+          cv = direct_entry<R>(tab, W, i, fv_r);
         } else {
           cu = lagrange_entry<R>(tab + ou_r + i, Wp, interp, fu_r);
           cv = lagrange_entry<R>(tab + ov_r + i, Wp, interp, fv_r);

@@ -132,6 +132,9 @@ class CSolver {
     return cholesky(L_, W_);
   }
 
+  // b <- A^-1 b (normal-equation route only).
+  void solve_A(double* b) const { cholesky_solve(L_, W_, b); }
+
   // C_j(s), j = 0..W-1, for offsets d_j = j - W/2 + s.
   bool solve(double s, double* c) const {
     const int K = nd_.K;
@@ -378,6 +381,50 @@ int build_least_misfit(int W, double x0p, int Ms, lmg_table* t) {
   return LMG_OK;
 }
 
+// Direct calculation (Section 5.2): A is Toeplitz and does not depend on s, so
+// C(s) = A^-1 B(s) with B_a(s) = sum_i w_i h_i cos(2 pi (a - W/2 + s) x_i). The nodes are
+// symmetric (x_{-k} = -x_k, h even), so B_a folds onto k = 0..Ng with weights omega_k and
+// angles theta_k = k phi, phi = 2 pi x0 / Ng; expanding cos(theta_k (a - W/2) + theta_k s)
+// gives C_a(s) = sum_k alpha[a][k] cos(k phi s) + beta[a][k] sin(k phi s) with
+// alpha[a][k] = sum_b Ainv[a][b] omega_k cos(theta_k (b - W/2)) and
+// beta[a][k] = -sum_b Ainv[a][b] omega_k sin(theta_k (b - W/2)).
+int direct_coefficients(const lmg_table* t, std::vector<double>& out) {
+  const int W = t->W, Kn = kNg + 1;
+  if (W > kDirectMaxW) return set_error(LMG_EUNSUPPORTED, "direct calculation needs W <= 11 (normal equations)");
+  if (t->h_nodes.size() != size_t(Kn) || !(t->h_nodes[0] > 0.0))
+    return set_error(LMG_EINVAL, "direct calculation needs a least-misfit table (h is unknown for caller tables)");
+  Nodes nd = make_nodes(t->x0p);
+  std::vector<double> h(nd.K);
+  for (int i = 0; i < nd.K; ++i) h[i] = t->h_nodes[size_t(std::abs(i - kNg))];
+  CSolver solver(nd, W);
+  if (!solver.set_h(h)) return set_error(LMG_ENOCONV, "direct calculation: A is not positive definite");
+  // A^-1, column by column through the Cholesky factor
+  std::vector<double> Ainv(size_t(W) * W);
+  for (int b = 0; b < W; ++b) {
+    std::vector<double> e(W, 0.0);
+    e[b] = 1.0;
+    solver.solve_A(e.data());
+    for (int a = 0; a < W; ++a) Ainv[size_t(a) * W + b] = e[a];
+  }
+  const double phi = kTwoPi * t->x0p / kNg;
+  out.assign(1 + size_t(2) * W * Kn, 0.0);
+  out[0] = phi;
+  for (int k = 0; k < Kn; ++k) {
+    const double omega = (k == 0 ? 1.0 : 2.0) * nd.w[size_t(kNg + k)] * h[size_t(kNg + k)];
+    for (int a = 0; a < W; ++a) {
+      double al = 0.0, be = 0.0;
+      for (int b = 0; b < W; ++b) {
+        const double th = k * phi * (b - 0.5 * W);
+        al += Ainv[size_t(a) * W + b] * omega * std::cos(th);
+        be -= Ainv[size_t(a) * W + b] * omega * std::sin(th);
+      }
+      out[1 + size_t(a) * Kn + k] = al;
+      out[1 + size_t(W + a) * Kn + k] = be;
+    }
+  }
+  return LMG_OK;
+}
+
 // c(x) = int_0^1 ds sum_j C_j(s) cos(2 pi d_j x), D(x) = int_0^1 ds |sum_j C_j(s) e^{i 2 pi d_j x}|^2
 // (Eqs. 12-14) for the interpolated table function; h = c / D (Eq. 15) or 1 / c.
 void correction_factors(const lmg_table* t, int64_t n_image, int64_t N, bool single_precision,
@@ -397,7 +444,10 @@ void correction_factors(const lmg_table* t, int64_t n_image, int64_t N, bool sin
   // the rows); beyond 4096 pieces, 4096 equal pieces (the kinks then sit far below
   // double-precision relevance).
   std::vector<double> edges;
-  if (Ms <= 4096) {
+  const bool direct = t->interp == LMG_INTERP_DIRECT;
+  if (direct) {  // the exact function is smooth in s: 64 equal pieces
+    for (int k = 0; k <= 64; ++k) edges.push_back(double(k) / 64);
+  } else if (Ms <= 4096) {
     if (t->interp == LMG_INTERP_LINEAR) {
       for (int k = 0; k <= Ms; ++k) edges.push_back(double(k) / Ms);
     } else if (t->interp == LMG_INTERP_NEAREST) {
@@ -412,6 +462,11 @@ void correction_factors(const lmg_table* t, int64_t n_image, int64_t N, bool sin
   }
   const size_t npieces = edges.size() - 1;
   std::vector<double> sn(npieces * 8), sw(npieces * 8), Cn(npieces * 8 * W);
+  Nodes nd = make_nodes(t->x0p);
+  std::vector<double> hfull(nd.K);
+  for (int i = 0; i < nd.K; ++i) hfull[i] = t->h_nodes.empty() ? 0.0 : t->h_nodes[size_t(std::abs(i - kNg))];
+  CSolver exact(nd, W);
+  if (direct) exact.set_h(hfull);
   for (size_t p = 0; p < npieces; ++p) {
     double lo = edges[p], hi = edges[p + 1], half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
     for (int g = 0; g < 8; ++g) {
@@ -419,7 +474,9 @@ void correction_factors(const lmg_table* t, int64_t n_image, int64_t N, bool sin
       double s = mid + half * gx[g];
       sn[q] = s;
       sw[q] = half * gw[g];
-      if (t->interp == LMG_INTERP_LINEAR) {
+      if (direct) {
+        exact.solve(s, &Cn[q * W]);
+      } else if (t->interp == LMG_INTERP_LINEAR) {
         double tt = s * Ms;
         int k = std::min(int(std::floor(tt)), Ms - 1);
         double f = tt - k;

@@ -13,7 +13,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "liblmg.so")
 
 LMG_C64, LMG_C128 = 0, 1
-INTERP = {"nearest": 0, "linear": 1, "quadratic": 2, "cubic": 3}
+INTERP = {"nearest": 0, "linear": 1, "quadratic": 2, "cubic": 3, "direct": 4}
 CORRECTION = {"hopt": 0, "inv_c": 1}
 ACCUM = {"plain": 0, "compensated": 1}
 LMG_CROP, LMG_PAD = 0, 1

@@ -43,7 +43,7 @@ def test_every_declared_function_is_exported_and_bound(lmg):
 @pytest.mark.parametrize("args,msg", [
     ((0, 0.5, 100, 1, 0), "W must be"), ((17, 0.5, 100, 1, 0), "W must be"),
     ((7, 0.0, 100, 1, 0), "x0 must be"), ((7, 1.5, 100, 1, 0), "x0 must be"),
-    ((7, 0.5, 1, 1, 0), "oversample"), ((7, 0.5, 100, 4, 0), "interp"), ((7, 0.5, 100, -1, 0), "interp"),
+    ((7, 0.5, 1, 1, 0), "oversample"), ((7, 0.5, 100, 5, 0), "interp"), ((7, 0.5, 100, -1, 0), "interp"),
     ((7, 0.5, 2, 3, 0), "at least the interpolation degree"), ((7, 0.5, 100, 1, 5), "correction")])
 def test_table_argument_errors(lmg, args, msg):
     h = ctypes.c_void_p()
@@ -161,3 +161,15 @@ def test_batch_argument_errors_precede_device_work(lmg):
     assert L.lmg_batch_bin(None, None, None, None) == -1
     assert L.lmg_batch_grid(None, None, None, None, None) == -1
     assert L.lmg_batch_info(None, None) == -1
+
+
+def test_direct_calculation_tables(lmg):
+    """LMG_INTERP_DIRECT (Section 5.2): a least-misfit table accepts it, a caller table does
+    not; its correction factors (from the exact function) agree with those of a finely
+    sampled cubic table of the same design."""
+    direct = lmg.Table(7, 0.5, 4, "direct")
+    cubic = lmg.Table(7, 0.5, 20000, "cubic")
+    hd, hc = direct.correction(256), cubic.correction(256)
+    assert np.abs(hd - hc).max() < 1e-12 * np.abs(hc).max()
+    with pytest.raises(lmg.LmgError, match="lmg_kernel_table"):
+        lmg.Table(4, 0.5, 64, "direct", values=np.ones((65, 4)))

@@ -247,3 +247,14 @@ def test_node_count_convergence():
     E32 = D.design_E(h_opt(7), 7, X0P)
     E64 = D.design_E(D.least_misfit_h(7, X0P, Ng=64), 7, X0P, Ng=64)
     assert abs(E64 - E32) < 0.1 * E32
+
+
+def test_direct_function_correction_matches_fine_table():
+    """Direct calculation (Section 5.2) uses the exact, smooth C(s): its correction factors
+    equal those of a finely sampled cubic table of the same design."""
+    W = 5
+    h = h_opt(W)
+    x = np.linspace(-0.25, 0.25, 33)
+    hd = D.correction_factors(lambda s: D.exact_C(h, W, X0P, s), None, None, W, x)
+    hc = D.correction_factors(D.lm_table(h, W, X0P, 4000), 4000, 3, W, x)
+    np.testing.assert_allclose(hd, hc, rtol=1e-12)
