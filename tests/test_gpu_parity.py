@@ -228,10 +228,14 @@ def test_fp32_higher_degree_tables(c2, interp, Ms):
 # ----------------------------------------------------------------------------------------
 # direct calculation (Section 5.2), float64
 # ----------------------------------------------------------------------------------------
-@pytest.mark.parametrize("W", [7, 11])
-def test_direct_calculation_matches_fine_cubic_table(W):
+@pytest.mark.parametrize("W,tol", [(7, 1e-11), (11, 1e-8)])
+def test_direct_calculation_matches_fine_cubic_table(W, tol):
     """Direct per-visibility weights against a finely sampled cubic table of the same design
-    (M_s = 20000, interpolation error far below 1e-11): grid and degrid agree to 1e-11."""
+    (M_s = 20000, interpolation error far below 1e-11). Both solve the normal equations,
+    whose matrix A grows ill-conditioned with W (Appendix B): the table row by row with a
+    Cholesky solve, the direct route through the folded A^-1. Each carries an error of
+    about cond(A) times the float64 epsilon, 1e-9 at W = 11, the largest W for which the
+    paper uses the normal equations; hence 1e-11 at W = 7 and 1e-8 at W = 11."""
     N, n_img, nvis = 256, 128, 4000
     uv, dl = disk_case(nvis, N, seed=50 + W)
     vis = S.complex_normal(nvis, 50 + W)
@@ -244,7 +248,7 @@ def test_direct_calculation_matches_fine_cubic_table(W):
                        p.degrid(to_dev(Gm, torch.complex128)).cpu().numpy())
     for k in range(2):
         a, b = out["direct"][k], out["cubic"][k]
-        assert np.abs(a - b).max() <= 1e-11 * np.abs(b).max()
+        assert np.abs(a - b).max() <= tol * np.abs(b).max()
 
 
 def test_direct_calculation_against_oracle():
