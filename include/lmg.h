@@ -259,7 +259,8 @@ int lmg_grid_static(const lmg_table* t, int64_t n_image, double pixel_scale, con
 
 /* lmg_batch_create -- per channel c: table tables[c] (not owned; must outlive the batch),
  * image size n_image[c], pixel scale pixel_scale[c] (radians) and capacity max_vis[c].
- * Same argument rules as lmg_plan_create for each channel; 1 <= n_chan <=
+ * Same argument rules as lmg_plan_create for each channel, with nearest or linear tables
+ * (LMG_EUNSUPPORTED otherwise); 1 <= n_chan <=
  * LMG_BATCH_MAX_CHANNELS. Allocates every channel's binning buffers, one work grid per
  * channel (contiguous per grid size) and one batched FFT plan per grid size. */
 int lmg_batch_create(int n_chan, const lmg_table* const* tables, const int64_t* n_image,

@@ -304,15 +304,15 @@ int plan_create(const lmg_table* t, int64_t n_image, double pixel_scale, int64_t
   p->smem_grid = sweep_smem_bytes(p->W, dtype, p->Ms, p->tab_smem_grid, false, p->warps_grid);
   p->smem_degrid = sweep_smem_bytes(p->W, dtype, p->Ms, p->tab_smem_degrid, true, p->warps_degrid);
   for (int accum = 0; accum <= (dtype == LMG_C64 ? 1 : 0); ++accum) {
-    if (sweep_set_smem_limits(p->W, dtype, accum, p->smem_grid, false) ||
-        sweep_occupancy(p->W, dtype, accum, p->smem_grid, false, p->warps_grid, &bps)) {
+    if (sweep_set_smem_limits(p->W, dtype, accum, p->smem_grid, false, p->interp >= 2) ||
+        sweep_occupancy(p->W, dtype, accum, p->smem_grid, false, p->interp >= 2, p->warps_grid, &bps)) {
       free_plan(p);
       return cuda_error(cudaGetLastError(), "sweep kernel attributes");
     }
     (accum ? p->blocks_grid_comp : p->blocks_grid) = p->sms * (bps > 0 ? bps : 1);
   }
-  if (sweep_set_smem_limits(p->W, dtype, 0, p->smem_degrid, true) ||
-      sweep_occupancy(p->W, dtype, 0, p->smem_degrid, true, p->warps_degrid, &bps)) {
+  if (sweep_set_smem_limits(p->W, dtype, 0, p->smem_degrid, true, p->interp >= 2) ||
+      sweep_occupancy(p->W, dtype, 0, p->smem_degrid, true, p->interp >= 2, p->warps_degrid, &bps)) {
     free_plan(p);
     return cuda_error(cudaGetLastError(), "sweep kernel attributes");
   }

@@ -529,8 +529,11 @@ int lmg_batch_create(int n_chan, const lmg_table* const* tables, const int64_t* 
   if (n_chan < 1 || n_chan > LMG_BATCH_MAX_CHANNELS)
     return set_error(LMG_EINVAL, "n_chan must be in [1, " + std::to_string(LMG_BATCH_MAX_CHANNELS) + "]");
   if (!tables || !n_image || !pixel_scale || !max_vis) return set_error(LMG_EINVAL, "NULL argument");
-  for (int c = 0; c < n_chan; ++c)
+  for (int c = 0; c < n_chan; ++c) {
     if (!tables[c]) return set_error(LMG_EINVAL, "tables[" + std::to_string(c) + "] is NULL");
+    if (tables[c]->interp > LMG_INTERP_LINEAR)
+      return set_error(LMG_EUNSUPPORTED, "batches run nearest or linear tables (tables[" + std::to_string(c) + "])");
+  }
   lmg_batch* b = new (std::nothrow) lmg_batch;
   if (!b) return set_error(LMG_ENOMEM, "host allocation failed");
   b->n_chan = n_chan;

@@ -78,8 +78,12 @@ int ring_slots(int W);
 int degrid_launch(const SweepArgs& a, cudaStream_t st);
 // Shared memory a sweep CTA needs (bytes) and CTAs per SM that fit; used to size launches.
 size_t sweep_smem_bytes(int W, int dtype, int Ms, bool table_in_smem, bool degrid, int warps);
-int sweep_set_smem_limits(int W, int dtype, int accum, size_t smem_bytes, bool degrid);
-int sweep_occupancy(int W, int dtype, int accum, size_t smem_bytes, bool degrid, int warps, int* blocks_per_sm);
+// ext: the kernels of the extended lookups (interp >= 2: Lagrange, direct calculation).
+int sweep_set_smem_limits(int W, int dtype, int accum, size_t smem_bytes, bool degrid, bool ext);
+int sweep_occupancy(int W, int dtype, int accum, size_t smem_bytes, bool degrid, bool ext, int warps,
+                    int* blocks_per_sm);
+// Kernel of the extended lookups (sweep_ext.cu).
+void* sweep_kernel_ext(int W, int dtype, int accum, bool degrid);
 // Warps per CTA and table placement so that a CTA's shared memory stays within `limit`.
 int sweep_config(int W, int dtype, int Ms, bool degrid, size_t limit, bool* table_in_smem, int* warps);
 

@@ -157,7 +157,9 @@ extern "C" int lmg_grid_static(const lmg_table* t, int64_t n_image, double pixel
   if (sweep_config(W, LMG_C64, Ms, false, 200 * 1024, &tab_smem, &warps))
     return set_error(LMG_EUNSUPPORTED, "sweep shared memory does not fit for this W");
   const size_t smem = sweep_smem_bytes(W, LMG_C64, Ms, tab_smem, false, warps);
-  if (sweep_set_smem_limits(W, LMG_C64, 0, smem, false) || sweep_occupancy(W, LMG_C64, 0, smem, false, warps, &bps))
+  const bool ext = t->interp >= 2;
+  if (sweep_set_smem_limits(W, LMG_C64, 0, smem, false, ext) ||
+      sweep_occupancy(W, LMG_C64, 0, smem, false, ext, warps, &bps))
     return set_error(LMG_ECUDA, std::string("sweep kernel attributes: ") + cudaGetErrorString(cudaGetLastError()));
   SweepArgs a{};
   a.recs = b.recs;

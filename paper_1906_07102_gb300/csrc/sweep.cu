@@ -1,23 +1,9 @@
-// Single-plan gridding and degridding kernels: persistent CTAs whose warps take work items
-// from a counter and run the per-item sweeps of sweep_body.cuh; the spill and fix-up passes;
-// launch configuration.
+// Single-plan gridding and degridding: the nearest / linear table kernels (the extended
+// lookups are compiled in sweep_ext.cu), the spill and fix-up passes, launch configuration.
 #include "sweep_body.cuh"
 
 namespace lmg {
 namespace {
-
-template <int W, typename R, bool COMP>
-__global__ void __launch_bounds__(kThreads, min_blocks<W, R, COMP>()) k_grid_sweep(const SweepArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const R* tab = stage_table<R>(a.table, (a.Ms + 1) * a.Wp, a.table_in_smem != 0, smem);
-  const size_t tab_bytes = a.table_in_smem ? align16(size_t(a.Ms + 1) * a.Wp * sizeof(R)) : 0;
-  unsigned char* my = smem + tab_bytes + warp * align16(Stage<W, R>::grid_bytes);
-  int nfront;
-  const int total = work_total(a.counters, a.item_cap, nfront);
-  for (int w = next_item(a.counters + kCntGridWork, lane); w < total; w = next_item(a.counters + kCntGridWork, lane))
-    grid_item<W, R, COMP>(a, tab, my, item_slot(w, nfront, a.item_cap), lane);
-}
 
 template <typename R>
 __global__ void k_grid_spill(const Item* __restrict__ items, const int* __restrict__ counters, int item_cap,
@@ -32,22 +18,6 @@ __global__ void k_grid_spill(const Item* __restrict__ items, const int* __restri
     spill_unit<R>(items, nfront, item_cap, W, RS, N, spill, grid, w, lane);
 }
 
-template <int W, typename R>
-__global__ void __launch_bounds__(kThreads, min_blocks<W, R>()) k_degrid_sweep(const SweepArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const R* tab = stage_table<R>(a.table, (a.Ms + 1) * a.Wp, a.table_in_smem != 0, smem);
-  const size_t tab_bytes = a.table_in_smem ? align16(size_t(a.Ms + 1) * a.Wp * sizeof(R)) : 0;
-  unsigned char* my = smem + tab_bytes + warp * align16(Stage<W, R>::degrid_bytes);
-  int nfront;
-  const int total = work_total(a.counters, a.item_cap, nfront);
-  for (int w = next_item(a.counters + kCntDegridWork, lane); w < total;
-       w = next_item(a.counters + kCntDegridWork, lane)) {
-    const Item item = a.items[item_slot(w, nfront, a.item_cap)];
-    degrid_item<W, R>(a, tab, my, item, lane);
-  }
-}
-
 template <typename R>
 __global__ void k_degrid_fixup(const VisPos* __restrict__ pos, long long nvis, int W,
                                const typename Cplx<R>::T* __restrict__ dpart, typename Cplx<R>::T* __restrict__ out) {
@@ -56,39 +26,8 @@ __global__ void k_degrid_fixup(const VisPos* __restrict__ pos, long long nvis, i
     fixup_one<R>(pos, k, W, dpart, out);
 }
 
-template <int W, typename R, bool COMP> void* grid_kernel_ptr() {
-  return reinterpret_cast<void*>(&k_grid_sweep<W, R, COMP>);
-}
-template <int W, typename R> void* degrid_kernel_ptr() {
-  return reinterpret_cast<void*>(&k_degrid_sweep<W, R>);
-}
-
-template <int W> void* pick_kernel(int dtype, int accum, bool degrid) {
-  if (degrid) return dtype ? degrid_kernel_ptr<W, double>() : degrid_kernel_ptr<W, float>();
-  if (dtype) return grid_kernel_ptr<W, double, false>();
-  return accum ? grid_kernel_ptr<W, float, true>() : grid_kernel_ptr<W, float, false>();
-}
-
-void* kernel_for(int W, int dtype, int accum, bool degrid) {
-  switch (W) {
-    case 1: return pick_kernel<1>(dtype, accum, degrid);
-    case 2: return pick_kernel<2>(dtype, accum, degrid);
-    case 3: return pick_kernel<3>(dtype, accum, degrid);
-    case 4: return pick_kernel<4>(dtype, accum, degrid);
-    case 5: return pick_kernel<5>(dtype, accum, degrid);
-    case 6: return pick_kernel<6>(dtype, accum, degrid);
-    case 7: return pick_kernel<7>(dtype, accum, degrid);
-    case 8: return pick_kernel<8>(dtype, accum, degrid);
-    case 9: return pick_kernel<9>(dtype, accum, degrid);
-    case 10: return pick_kernel<10>(dtype, accum, degrid);
-    case 11: return pick_kernel<11>(dtype, accum, degrid);
-    case 12: return pick_kernel<12>(dtype, accum, degrid);
-    case 13: return pick_kernel<13>(dtype, accum, degrid);
-    case 14: return pick_kernel<14>(dtype, accum, degrid);
-    case 15: return pick_kernel<15>(dtype, accum, degrid);
-    case 16: return pick_kernel<16>(dtype, accum, degrid);
-    default: return nullptr;
-  }
+void* kernel_for(int W, int dtype, int accum, bool degrid, bool ext) {
+  return ext ? sweep_kernel_ext(W, dtype, accum, degrid) : sweep_kernel_pick<false>(W, dtype, accum, degrid);
 }
 
 }  // namespace
@@ -102,14 +41,15 @@ size_t sweep_smem_bytes(int W, int dtype, int Ms, bool table_in_smem, bool degri
   return tab + size_t(warps) * stage_bytes(W, dtype, degrid);
 }
 
-int sweep_set_smem_limits(int W, int dtype, int accum, size_t smem_bytes, bool degrid) {
-  void* k = kernel_for(W, dtype, accum, degrid);
+int sweep_set_smem_limits(int W, int dtype, int accum, size_t smem_bytes, bool degrid, bool ext) {
+  void* k = kernel_for(W, dtype, accum, degrid, ext);
   if (!k) return -1;
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_bytes)) == cudaSuccess ? 0 : -1;
 }
 
-int sweep_occupancy(int W, int dtype, int accum, size_t smem_bytes, bool degrid, int warps, int* blocks_per_sm) {
-  void* k = kernel_for(W, dtype, accum, degrid);
+int sweep_occupancy(int W, int dtype, int accum, size_t smem_bytes, bool degrid, bool ext, int warps,
+                    int* blocks_per_sm) {
+  void* k = kernel_for(W, dtype, accum, degrid, ext);
   if (!k) return -1;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, 32 * warps, smem_bytes) == cudaSuccess ? 0
                                                                                                                 : -1;
@@ -132,7 +72,7 @@ int sweep_config(int W, int dtype, int Ms, bool degrid, size_t limit, bool* tabl
 }
 
 int grid_launch(const SweepArgs& a, cudaStream_t st) {
-  void* k = kernel_for(a.W, a.dtype, a.accum, false);
+  void* k = kernel_for(a.W, a.dtype, a.accum, false, a.interp >= 2);
   if (!k) return -1;
   const size_t smem = sweep_smem_bytes(a.W, a.dtype, a.Ms, a.table_in_smem != 0, false, a.warps);
   cudaMemsetAsync(a.counters + kCntGridWork, 0, sizeof(int), st);
@@ -153,7 +93,7 @@ int grid_launch(const SweepArgs& a, cudaStream_t st) {
 }
 
 int degrid_launch(const SweepArgs& a, cudaStream_t st) {
-  void* k = kernel_for(a.W, a.dtype, 0, true);
+  void* k = kernel_for(a.W, a.dtype, 0, true, a.interp >= 2);
   if (!k) return -1;
   const size_t smem = sweep_smem_bytes(a.W, a.dtype, a.Ms, a.table_in_smem != 0, true, a.warps);
   cudaMemsetAsync(a.counters + kCntDegridWork, 0, sizeof(int), st);

@@ -85,15 +85,17 @@ template <int W, typename R> struct Stage {
 // of coordinate S (units of 2^-32), from the exact integer product S Ms. Linear uses row
 // k = floor(t) and fraction t - k with t = S Ms 2^-32; nearest uses row floor(t + 1/2). The
 // table has Ms + 1 rows of stride Wp.
-template <typename R>
+template <typename R, bool EXT>
 __device__ __forceinline__ void table_coord(int Wp, int Ms, int interp, unsigned S, int& off, R& f) {
   const unsigned long long Pm = static_cast<unsigned long long>(S) * static_cast<unsigned>(Ms);
-  if (interp == 1) {
-    off = static_cast<int>(Pm >> 32) * Wp;
-    f = static_cast<R>(static_cast<unsigned>(Pm & 0xffffffffull)) * static_cast<R>(2.3283064365386962890625e-10);
-  } else if (interp == 0) {
-    off = static_cast<int>((Pm + 0x80000000ull) >> 32) * Wp;
-    f = R(0);
+  if constexpr (!EXT) {
+    if (interp) {
+      off = static_cast<int>(Pm >> 32) * Wp;
+      f = static_cast<R>(static_cast<unsigned>(Pm & 0xffffffffull)) * static_cast<R>(2.3283064365386962890625e-10);
+    } else {
+      off = static_cast<int>((Pm + 0x80000000ull) >> 32) * Wp;
+      f = R(0);
+    }
   } else if (interp == 4) {
     // direct calculation: the coefficients replace the rows; f = s
     off = 0;
@@ -147,7 +149,7 @@ __device__ __forceinline__ R lagrange_entry(const R* __restrict__ p, int Wp, int
 // a record and compute one table entry each (C = T[k] + f (T[k+1] - T[k]), or Lagrange
 // through d + 1 rows), so a round's
 // table reads touch P rows instead of 32 rows per instruction.
-template <int W, typename R, bool GRID>
+template <int W, typename R, bool GRID, bool EXT>
 __device__ __forceinline__ void stage_chunk(const R* __restrict__ tab, int Wp, int interp, int lo, int hi, int ou,
                                             R fu, int ov, R fv, int d, R wx, R wy, R* __restrict__ s_cv,
                                             void* __restrict__ s_u, int lane) {
@@ -170,19 +172,27 @@ __device__ __forceinline__ void stage_chunk(const R* __restrict__ tab, int Wp, i
     if (r < hi) {
       if (i < W) {
         R cu, cv;
-        if (interp <= 1) {
+        if constexpr (!EXT) {
           cu = tab[ou_r + i];
           cv = tab[ov_r + i];
           if (interp) {
             cu = cu + fu_r * (tab[ou_r + Wp + i] - cu);
             cv = cv + fv_r * (tab[ov_r + Wp + i] - cv);
           }
-        } else if (interp == 4) {
-          cu = direct_entry<R>(tab, W, i, fu_r);
-          cv = direct_entry<R>(tab, W, i, fv_r);
         } else {
-          cu = lagrange_entry<R>(tab + ou_r + i, Wp, interp, fu_r);
-          cv = lagrange_entry<R>(tab + ov_r + i, Wp, interp, fv_r);
+          // direct calculation exists for float64 plans and W <= 11 only (plan creation)
+          if constexpr (sizeof(R) == 8 && W <= 11) {
+            if (interp == 4) {
+              cu = direct_entry<R>(tab, W, i, fu_r);
+              cv = direct_entry<R>(tab, W, i, fv_r);
+            } else {
+              cu = lagrange_entry<R>(tab + ou_r + i, Wp, interp, fu_r);
+              cv = lagrange_entry<R>(tab + ov_r + i, Wp, interp, fv_r);
+            }
+          } else {
+            cu = lagrange_entry<R>(tab + ou_r + i, Wp, interp, fu_r);
+            cv = lagrange_entry<R>(tab + ov_r + i, Wp, interp, fv_r);
+          }
         }
         if constexpr (GRID) {
           C2 t;
@@ -243,14 +253,15 @@ __device__ __forceinline__ void two_sum_acc(float& a, float& lo, float b) {
 }
 
 // Resident CTAs per SM the register allocation must allow.
-template <int W, typename R, bool COMP = false> constexpr int min_blocks() {
-  return COMP ? 2 : ((sizeof(R) == 4 && W <= 8) ? 3 : 1);
+template <int W, typename R, bool COMP = false, bool EXT = false> constexpr int min_blocks() {
+  // the extended lookups (Lagrange, direct) need more registers: fewer resident CTAs
+  return COMP ? 2 : ((sizeof(R) == 4 && W <= 8) ? (EXT ? 2 : 3) : 1);
 }
 
 
 // One gridding work item (rows [r0, r1) of one strip), run by the 32 lanes of a warp;
 // `my` is the warp's staging area in shared memory, `tab` the table (shared or global).
-template <int W, typename R, bool COMP>
+template <int W, typename R, bool COMP, bool EXT = false>
 __device__ __forceinline__ void grid_item(const SweepArgs& a, const R* __restrict__ tab, unsigned char* my,
                                           int slot, int lane) {
   using C2 = typename Cplx<R>::T;
@@ -316,9 +327,9 @@ __device__ __forceinline__ void grid_item(const SweepArgs& a, const R* __restric
           if (mine) s_x0[lane] = xrel;
           int ou, ov;
           R fu, fv;
-          table_coord<R>(Wp, a.Ms, a.interp, f0.rc.su, ou, fu);
-          table_coord<R>(Wp, a.Ms, a.interp, f0.rc.sv, ov, fv);
-          stage_chunk<W, R, true>(tab, Wp, a.interp, lo, hi, ou, fu, ov, fv, rec_row(f0.rc.rx) - row0,
+          table_coord<R, EXT>(Wp, a.Ms, a.interp, f0.rc.su, ou, fu);
+          table_coord<R, EXT>(Wp, a.Ms, a.interp, f0.rc.sv, ov, fv);
+          stage_chunk<W, R, true, EXT>(tab, Wp, a.interp, lo, hi, ou, fu, ov, fv, rec_row(f0.rc.rx) - row0,
                                   f0.v.x * f0.wt, f0.v.y * f0.wt, s_cv, s_a, lane);
           const unsigned cover = mine ? cover_mask(xrel, W) : 0u;
           __syncwarp();
@@ -426,7 +437,7 @@ __device__ __forceinline__ void spill_unit(const Item* __restrict__ items, int n
 }
 
 // One degridding work item, run by the 32 lanes of a warp (see grid_item).
-template <int W, typename R>
+template <int W, typename R, bool EXT = false>
 __device__ __forceinline__ void degrid_item(const SweepArgs& a, const R* __restrict__ tab, unsigned char* my,
                                             const Item& item, int lane) {
   using C2 = typename Cplx<R>::T;
@@ -489,9 +500,9 @@ __device__ __forceinline__ void degrid_item(const SweepArgs& a, const R* __restr
           if (mine) s_x0[lane] = xrel;
           int ou, ov;
           R fu, fv;
-          table_coord<R>(Wp, a.Ms, a.interp, rc0.su, ou, fu);
-          table_coord<R>(Wp, a.Ms, a.interp, rc0.sv, ov, fv);
-          stage_chunk<W, R, false>(tab, Wp, a.interp, lo, hi, ou, fu, ov, fv, rec_row(rc0.rx) - row0, R(0), R(0),
+          table_coord<R, EXT>(Wp, a.Ms, a.interp, rc0.su, ou, fu);
+          table_coord<R, EXT>(Wp, a.Ms, a.interp, rc0.sv, ov, fv);
+          stage_chunk<W, R, false, EXT>(tab, Wp, a.interp, lo, hi, ou, fu, ov, fv, rec_row(rc0.rx) - row0, R(0), R(0),
                                    s_cv, s_cu, lane);
           const unsigned cover = mine ? cover_mask(xrel, W) : 0u;
           __syncwarp();
@@ -599,6 +610,69 @@ __device__ __forceinline__ void fixup_one(const VisPos* __restrict__ pos, long l
     v.x += p.x;
     v.y += p.y;
     out[k] = v;
+  }
+}
+
+// Persistent single-plan sweep kernels: each warp takes work items from a counter and runs
+// the per-item sweep. EXT selects the extended lookups (Lagrange, direct calculation),
+// compiled separately so that the nearest / linear kernels keep their register budget.
+template <int W, typename R, bool COMP, bool EXT>
+__global__ void __launch_bounds__(kThreads, min_blocks<W, R, COMP, EXT>()) k_grid_sweep(const SweepArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const R* tab = stage_table<R>(a.table, (a.Ms + 1) * a.Wp, a.table_in_smem != 0, smem);
+  const size_t tab_bytes = a.table_in_smem ? align16(size_t(a.Ms + 1) * a.Wp * sizeof(R)) : 0;
+  unsigned char* my = smem + tab_bytes + warp * align16(Stage<W, R>::grid_bytes);
+  int nfront;
+  const int total = work_total(a.counters, a.item_cap, nfront);
+  for (int w = next_item(a.counters + kCntGridWork, lane); w < total; w = next_item(a.counters + kCntGridWork, lane))
+    grid_item<W, R, COMP, EXT>(a, tab, my, item_slot(w, nfront, a.item_cap), lane);
+}
+
+template <int W, typename R, bool EXT>
+__global__ void __launch_bounds__(kThreads, min_blocks<W, R, false, EXT>()) k_degrid_sweep(const SweepArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const R* tab = stage_table<R>(a.table, (a.Ms + 1) * a.Wp, a.table_in_smem != 0, smem);
+  const size_t tab_bytes = a.table_in_smem ? align16(size_t(a.Ms + 1) * a.Wp * sizeof(R)) : 0;
+  unsigned char* my = smem + tab_bytes + warp * align16(Stage<W, R>::degrid_bytes);
+  int nfront;
+  const int total = work_total(a.counters, a.item_cap, nfront);
+  for (int w = next_item(a.counters + kCntDegridWork, lane); w < total;
+       w = next_item(a.counters + kCntDegridWork, lane)) {
+    const Item item = a.items[item_slot(w, nfront, a.item_cap)];
+    degrid_item<W, R, EXT>(a, tab, my, item, lane);
+  }
+}
+
+template <bool EXT, int W> void* pick_sweep_kernel(int dtype, int accum, bool degrid) {
+  if (degrid)
+    return dtype ? reinterpret_cast<void*>(&k_degrid_sweep<W, double, EXT>)
+                 : reinterpret_cast<void*>(&k_degrid_sweep<W, float, EXT>);
+  if (dtype) return reinterpret_cast<void*>(&k_grid_sweep<W, double, false, EXT>);
+  return accum ? reinterpret_cast<void*>(&k_grid_sweep<W, float, true, EXT>)
+               : reinterpret_cast<void*>(&k_grid_sweep<W, float, false, EXT>);
+}
+
+template <bool EXT> void* sweep_kernel_pick(int W, int dtype, int accum, bool degrid) {
+  switch (W) {
+    case 1: return pick_sweep_kernel<EXT, 1>(dtype, accum, degrid);
+    case 2: return pick_sweep_kernel<EXT, 2>(dtype, accum, degrid);
+    case 3: return pick_sweep_kernel<EXT, 3>(dtype, accum, degrid);
+    case 4: return pick_sweep_kernel<EXT, 4>(dtype, accum, degrid);
+    case 5: return pick_sweep_kernel<EXT, 5>(dtype, accum, degrid);
+    case 6: return pick_sweep_kernel<EXT, 6>(dtype, accum, degrid);
+    case 7: return pick_sweep_kernel<EXT, 7>(dtype, accum, degrid);
+    case 8: return pick_sweep_kernel<EXT, 8>(dtype, accum, degrid);
+    case 9: return pick_sweep_kernel<EXT, 9>(dtype, accum, degrid);
+    case 10: return pick_sweep_kernel<EXT, 10>(dtype, accum, degrid);
+    case 11: return pick_sweep_kernel<EXT, 11>(dtype, accum, degrid);
+    case 12: return pick_sweep_kernel<EXT, 12>(dtype, accum, degrid);
+    case 13: return pick_sweep_kernel<EXT, 13>(dtype, accum, degrid);
+    case 14: return pick_sweep_kernel<EXT, 14>(dtype, accum, degrid);
+    case 15: return pick_sweep_kernel<EXT, 15>(dtype, accum, degrid);
+    case 16: return pick_sweep_kernel<EXT, 16>(dtype, accum, degrid);
+    default: return nullptr;
   }
 }
 
