@@ -68,7 +68,7 @@ namespace lmg {
 void free_plan(lmg_plan* p) {
   if (!p) return;
   void* ptrs[] = {p->d_table, p->d_h, p->pos, p->hist, p->offsets, p->rank, p->partial, p->recs,
-                  p->items, p->counters, p->spill, p->dpart, p->work};
+                  p->items, p->counters, p->spill, p->work};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->fft_ok) cufftDestroy(p->fft);
@@ -135,7 +135,6 @@ int do_degrid(lmg_plan* p, const void* grid, void* vis_out, cudaStream_t st) {
   SweepArgs a = sweep_args(p);
   a.grid_in = grid;
   a.vis_out = vis_out;
-  a.dpart = p->dpart;
   a.grid_blocks = p->blocks_degrid;
   a.warps = p->warps_degrid;
   a.table_in_smem = p->tab_smem_degrid ? 1 : 0;
@@ -281,7 +280,6 @@ int plan_create(const lmg_table* t, int64_t n_image, double pixel_scale, int64_t
       (rc = dalloc(&p->partial, size_t(p->nchunks), "scan")) || (rc = dalloc(&p->recs, size_t(2 * max_vis), "records")) ||
       (rc = dalloc(&p->items, size_t(p->item_cap), "items")) || (rc = dalloc(&p->counters, kNumCounters, "counters")) ||
       (rc = dalloc(reinterpret_cast<unsigned char**>(&p->spill), size_t(p->item_cap) * ring_slots(p->W) * kStrip * c2, "spill")) ||
-      (rc = dalloc(reinterpret_cast<unsigned char**>(&p->dpart), size_t(max_vis) * c2, "partials")) ||
       (opt.work_grid && (rc = dalloc(reinterpret_cast<unsigned char**>(&p->work), size_t(N) * size_t(N) * c2, "work grid")))) {
     free_plan(p);
     return rc;

@@ -6,8 +6,8 @@
 // W; channels of every grid size and visibility count share it): its warps take work
 // indices from one counter, a work index maps through the per-channel prefix of item counts
 // to (channel, item), and the item runs the same per-item code as the single-plan sweep.
-// Spill rows and the degridding fix-up run as one launch per W class (blockIdx.y =
-// channel); FFTs run as one batched cuFFT plan per distinct grid size. Each operation's launch sequence is
+// Spill rows and the zeroing of degridding outputs run as one launch per W class
+// (blockIdx.y = channel); FFTs run as one batched cuFFT plan per distinct grid size. Each operation's launch sequence is
 // captured once into a CUDA graph on the batch's own stream and replayed while the caller's
 // buffers stay the same. Bin sizes, item sizes, warps per CTA and the table placement are
 // chosen by a small autotuner that times the candidates on the caller's data.
@@ -153,12 +153,14 @@ __global__ void k_batch_spill(const BatchChan* __restrict__ ch) {
                       static_cast<float2*>(a.grid), w, lane);
 }
 
-// Degridding fix-up of every channel (blockIdx.y = channel).
-__global__ void k_batch_fixup(const BatchChan* __restrict__ ch) {
+// Zeroes every channel's degridding output before the sweep (blockIdx.y = channel): each
+// record adds its partial sum, dropped positions stay zero.
+__global__ void k_batch_zero(const BatchChan* __restrict__ ch) {
   const SweepArgs a = ch[blockIdx.y].a;
+  float2* out = static_cast<float2*>(a.vis_out);
   const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
   for (long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; k < a.nvis; k += stride)
-    fixup_one<float>(a.pos, k, a.W, static_cast<const float2*>(a.dpart), static_cast<float2*>(a.vis_out));
+    out[k] = make_float2(0.f, 0.f);
 }
 
 // Crop + correct of every channel (blockIdx.y = channel); same arithmetic as the
@@ -380,7 +382,6 @@ int fill_sweeps(lmg_batch* b, int op, const void* const* in, const void* const* 
       } else {
         a.grid_in = op == kOpDegrid ? in[c] : b->work[size_t(c)];
         a.vis_out = out[c];
-        a.dpart = p->dpart;
       }
       h[j].a = a;
       h[j].tab_off = k.tab_off[j];
@@ -429,10 +430,10 @@ int launch_sweeps(lmg_batch* b, int op, cudaStream_t s) {
     int tab_floats = k.tab_floats;
     int tab_in_smem = (b->tab_smem && k.tab_fits) ? 1 : 0;
     void* params[] = {&ch, &prefix, &n_chan, &work, &tables, &tab_floats, &tab_in_smem};
+    if (degrid) k_batch_zero<<<dim3(2 * b->sms, n), 256, 0, s>>>(k.d_desc[op]);
     e = cudaLaunchKernel(batch_kernel_for(k.W, degrid), dim3(k.blocks[d]), dim3(32 * b->warps), params, k.smem[d], s);
     if (e != cudaSuccess) return cuda_error(e, "batch: sweep launch");
     if (!degrid) k_batch_spill<<<dim3(2 * b->sms, n), 256, 0, s>>>(k.d_desc[op]);
-    else k_batch_fixup<<<dim3(4 * b->sms, n), 256, 0, s>>>(k.d_desc[op]);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "batch: spill / fix-up launch");
   }
   return LMG_OK;

@@ -67,7 +67,6 @@ struct SweepArgs {
   // degridding
   const void* grid_in;
   void* vis_out;
-  void* dpart;        // max_vis complex (secondary partial sums)
   const VisPos* pos;  // per visibility support start (x0 < 0: dropped)
   long long nvis;
 };

@@ -77,7 +77,6 @@ struct lmg_plan {
   lmg::Item* items = nullptr;
   int* counters = nullptr;
   void* spill = nullptr;
-  void* dpart = nullptr;
   void* work = nullptr;      // N x N work grid (null in batch channels)
   cufftHandle fft = 0;              // full 2-D transform (lmg_fft)
   bool fft_ok = false;

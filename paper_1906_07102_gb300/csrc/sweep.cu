@@ -1,5 +1,5 @@
 // Single-plan gridding and degridding: the nearest / linear table kernels (the extended
-// lookups are compiled in sweep_ext.cu), the spill and fix-up passes, launch configuration.
+// lookups are compiled in sweep_ext.cu), the spill pass, launch configuration.
 #include "sweep_body.cuh"
 
 namespace lmg {
@@ -16,14 +16,6 @@ __global__ void k_grid_spill(const Item* __restrict__ items, const int* __restri
   const long long n = static_cast<long long>(total) * RS;
   for (long long w = gw; w < n; w += (static_cast<long long>(gridDim.x) * blockDim.x) >> 5)
     spill_unit<R>(items, nfront, item_cap, W, RS, N, spill, grid, w, lane);
-}
-
-template <typename R>
-__global__ void k_degrid_fixup(const VisPos* __restrict__ pos, long long nvis, int W,
-                               const typename Cplx<R>::T* __restrict__ dpart, typename Cplx<R>::T* __restrict__ out) {
-  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
-  for (long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; k < nvis; k += stride)
-    fixup_one<R>(pos, k, W, dpart, out);
 }
 
 void* kernel_for(int W, int dtype, int accum, bool degrid, bool ext) {
@@ -96,19 +88,12 @@ int degrid_launch(const SweepArgs& a, cudaStream_t st) {
   void* k = kernel_for(a.W, a.dtype, 0, true, a.interp >= 2);
   if (!k) return -1;
   const size_t smem = sweep_smem_bytes(a.W, a.dtype, a.Ms, a.table_in_smem != 0, true, a.warps);
+  // outputs start at zero: each record adds its partial sum (dropped positions stay zero)
+  if (a.nvis > 0) cudaMemsetAsync(a.vis_out, 0, size_t(a.nvis) * (a.dtype ? 16 : 8), st);
   cudaMemsetAsync(a.counters + kCntDegridWork, 0, sizeof(int), st);
   SweepArgs args = a;
   void* params[] = {&args};
   if (cudaLaunchKernel(k, dim3(a.grid_blocks), dim3(32 * a.warps), params, smem, st) != cudaSuccess) return -1;
-  if (a.dtype) {
-    k_degrid_fixup<double><<<8 * 152, 256, 0, st>>>(a.pos, a.nvis, a.W,
-                                                    static_cast<const double2*>(a.dpart),
-                                                    static_cast<double2*>(a.vis_out));
-  } else {
-    k_degrid_fixup<float><<<8 * 152, 256, 0, st>>>(a.pos, a.nvis, a.W,
-                                                   static_cast<const float2*>(a.dpart),
-                                                   static_cast<float2*>(a.vis_out));
-  }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

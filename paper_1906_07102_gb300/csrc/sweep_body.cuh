@@ -26,7 +26,8 @@
 //      all items have stored their rows.
 //      degridding: the ring holds grid rows of the lane's column; lane t forms
 //      Cu_i sum_q Cv'_q G[row0 + q][t] for each covering record and stages it; lane l sums
-//      its record's W partial sums.
+//      its record's partial sums and adds the result to the zeroed output (a visibility
+//      whose support crosses a strip has two records, one per strip).
 // Every grid cell is written exactly once by the gridding sweep (no pre-zeroing, no
 #pragma once
 
@@ -453,7 +454,6 @@ __device__ __forceinline__ void degrid_item(const SweepArgs& a, const R* __restr
   const Rec* __restrict__ recs = a.recs;
   const C2* __restrict__ G = static_cast<const C2*>(a.grid_in);
   C2* __restrict__ out = static_cast<C2*>(a.vis_out);
-  C2* __restrict__ dpart = static_cast<C2*>(a.dpart);
   const int N = a.N;
 
   if (item.nrec == 0) return;
@@ -575,8 +575,9 @@ __device__ __forceinline__ void degrid_item(const SweepArgs& a, const R* __restr
             C2 o;
             o.x = vr;
             o.y = vi;
-            if (xrel >= 0) out[rc0.idx] = o;
-            else dpart[rc0.idx] = o;
+            // both records of a visibility crossing a strip add into the zeroed output
+            // (two terms onto zero: the sum does not depend on their order)
+            red_add(out + rc0.idx, o);
           }
           __syncwarp();
           cstart = ce;
@@ -589,27 +590,6 @@ __device__ __forceinline__ void degrid_item(const SweepArgs& a, const R* __restr
         }
       }
     }
-  }
-}
-
-// Visibility k after the degridding sweep: adds the partial sum of its secondary record
-// (support crossing a strip boundary) or zeroes the output of a dropped position.
-template <typename R>
-__device__ __forceinline__ void fixup_one(const VisPos* __restrict__ pos, long long k, int W,
-                                          const typename Cplx<R>::T* __restrict__ dpart,
-                                          typename Cplx<R>::T* __restrict__ out) {
-  const int x0 = pos[k].x0;
-  if (x0 < 0) {
-    typename Cplx<R>::T z;
-    z.x = 0;
-    z.y = 0;
-    out[k] = z;
-  } else if ((x0 % kStrip) + W > kStrip) {
-    auto v = out[k];
-    const auto p = dpart[k];
-    v.x += p.x;
-    v.y += p.y;
-    out[k] = v;
   }
 }
 
