@@ -664,7 +664,7 @@ def run_autograd(args):
             "clocks": clk,
             "e2e": {"value": nv / (ms_e * 1e-3) / 1e6, "unit": "Mvis/s",
                     "h2d_bytes_per_step": image.nbytes + V.nbytes, "d2h_bytes_per_step": image.nbytes},
-            "gpu_launches": 6 * args.steps}
+            "gpu_launches": 5 * args.steps}
     print(json.dumps(line), flush=True)
 
 
