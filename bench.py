@@ -58,6 +58,23 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(ms, device):
+    """The slowest rank's time: replicas run the same work, the job ends with the last one
+    (all-reduce MAX over the process group; the value itself on one process)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mvis(nvis_per_rank, world, ms):
+    """Visibilities processed by all ranks per second, in millions."""
+    return world * nvis_per_rank / (ms * 1e-3) / 1e6
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -319,12 +336,8 @@ def run_native(args):
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    step_ms = float(np.mean([s.elapsed_time(e) for s, e in zip(starts, ends)]))
-    if world > 1:
-        t = torch.tensor([step_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        step_ms = float(t.item())
-    value = world * nv / (step_ms * 1e-3) / 1e6
+    step_ms = max_over_ranks(float(np.mean([s.elapsed_time(e) for s, e in zip(starts, ends)])), dev)
+    value = whole_job_mvis(nv, world, step_ms)
 
     # per-stage breakdown (untimed by the driver's clock; same stream, events per stage)
     stages = {}
@@ -375,11 +388,7 @@ def run_native(args):
         e2e_step()
     ee.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = es.elapsed_time(ee) / ek
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(es.elapsed_time(ee) / ek, dev)
     h2d = uv_h.numel() * 8 + vis_h.numel() * 8 + model_h.numel() * 8
     d2h = img_h.numel() * 8 + pv_h.numel() * 8
 
@@ -404,7 +413,7 @@ def run_native(args):
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "flushed before every timed step (256 MB write, outside the step's events)"},
             "roofline": roof, "clocks": clk,
-            "e2e": {"value": world * nv / (e2e_ms * 1e-3) / 1e6, "unit": "Mvis/s", "h2d_bytes_per_step": h2d,
+            "e2e": {"value": whole_job_mvis(nv, world, e2e_ms), "unit": "Mvis/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": KERNELS_PER_STEP * args.steps}
     line.update(extra)
