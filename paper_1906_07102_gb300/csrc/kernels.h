@@ -17,7 +17,7 @@ struct Item;
 enum {
   kCntBad = 0,         // dropped positions
   kCntItems = 1,       // items placed from the front (heavy)
-  kCntSecondary = 2,   // unused
+  // slot 2 is free
   kCntItemsBack = 3,   // items placed from the back (light)
   kCntGridWork = 4,    // work counter of the gridding sweep
   kCntDegridWork = 5,  // work counter of the degridding sweep
