@@ -362,6 +362,9 @@ def run_native(args):
     timed("pad_correct", lambda: plan.pad_correct(model_d, out=work))
     timed("fft_model", lambda: plan.fft(work, "model", pruned=True))
     timed("degrid", lambda: plan.degrid(work, out=pv_d))
+    # the two public calls of a step, as a whole (prediction pads only the kept rows)
+    timed("dirty_image", lambda: plan.dirty_image(vis_d, out=img_d))
+    timed("predict_vis", lambda: plan.predict_vis(model_d, out=pv_d))
 
     # end to end through the public API with pinned host buffers
     uv_h = torch.from_numpy(uv).pin_memory()

@@ -211,7 +211,9 @@ int lmg_plan_info(lmg_plan* p, int64_t* out, void* stream);
 /* lmg_work_grid -- device pointer of the plan's internal [N][N] work grid (valid until
  * lmg_plan_free). lmg_dirty_image and lmg_predict_vis transform it with FFTs pruned to
  * the outputs they use: afterwards it holds the transform at the kept rows and columns
- * (dirty image) or the full model grid (prediction). */
+ * (dirty image) or the transformed model grid (prediction; the plan pads the model into a
+ * second internal grid whose rows outside the kept field stay zero and transforms it out of
+ * place into the work grid). */
 void* lmg_work_grid(lmg_plan* p);
 
 /* lmg_grid_static -- binning plus gridding (the work of lmg_plan_bin + lmg_grid, complex64)

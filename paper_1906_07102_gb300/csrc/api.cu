@@ -68,7 +68,7 @@ namespace lmg {
 void free_plan(lmg_plan* p) {
   if (!p) return;
   void* ptrs[] = {p->d_table, p->d_h, p->pos, p->hist, p->offsets, p->rank, p->partial, p->recs,
-                  p->items, p->counters, p->spill, p->work};
+                  p->items, p->counters, p->spill, p->work, p->model};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->fft_ok) cufftDestroy(p->fft);
@@ -181,6 +181,25 @@ int fft_image_pruned(lmg_plan* p, void* g, cudaStream_t st) {
   return rc;
 }
 
+// Model transform of lmg_predict_vis: rows of the kept rows in place in the model buffer
+// (its other rows stay zero), then every column out of place into the work grid.
+int fft_model_to_work(lmg_plan* p, cudaStream_t st) {
+  const size_t N = size_t(p->N), half = size_t(p->n_image / 2);
+  int rc = exec_1d(p, p->fft_rows_half, p->model, 0, CUFFT_FORWARD, st);
+  if (rc == LMG_OK) rc = exec_1d(p, p->fft_rows_half, p->model, (N - half) * N, CUFFT_FORWARD, st);
+  if (rc != LMG_OK) return rc;
+  if (cufftSetStream(p->fft_cols_all, st) != CUFFT_SUCCESS) return set_error(LMG_ECUFFT, "cufftSetStream failed");
+  cufftResult r;
+  if (p->dtype == LMG_C128)
+    r = cufftExecZ2Z(p->fft_cols_all, static_cast<cufftDoubleComplex*>(p->model), static_cast<cufftDoubleComplex*>(p->work),
+                     CUFFT_FORWARD);
+  else
+    r = cufftExecC2C(p->fft_cols_all, static_cast<cufftComplex*>(p->model), static_cast<cufftComplex*>(p->work),
+                     CUFFT_FORWARD);
+  if (r != CUFFT_SUCCESS) return set_error(LMG_ECUFFT, "cuFFT execution failed (code " + std::to_string(int(r)) + ")");
+  return LMG_OK;
+}
+
 int fft_model_pruned(lmg_plan* p, void* g, cudaStream_t st) {
   const size_t N = size_t(p->N), half = size_t(p->n_image / 2);
   int rc = exec_1d(p, p->fft_rows_half, g, 0, CUFFT_FORWARD, st);
@@ -280,13 +299,15 @@ int plan_create(const lmg_table* t, int64_t n_image, double pixel_scale, int64_t
       (rc = dalloc(&p->partial, size_t(p->nchunks), "scan")) || (rc = dalloc(&p->recs, size_t(2 * max_vis), "records")) ||
       (rc = dalloc(&p->items, size_t(p->item_cap), "items")) || (rc = dalloc(&p->counters, kNumCounters, "counters")) ||
       (rc = dalloc(reinterpret_cast<unsigned char**>(&p->spill), size_t(p->item_cap) * ring_slots(p->W) * kStrip * c2, "spill")) ||
-      (opt.work_grid && (rc = dalloc(reinterpret_cast<unsigned char**>(&p->work), size_t(N) * size_t(N) * c2, "work grid")))) {
+      (opt.work_grid && (rc = dalloc(reinterpret_cast<unsigned char**>(&p->work), size_t(N) * size_t(N) * c2, "work grid"))) ||
+      (opt.work_grid && (rc = dalloc(reinterpret_cast<unsigned char**>(&p->model), size_t(N) * size_t(N) * c2, "model grid")))) {
     free_plan(p);
     return rc;
   }
   if ((e = cudaMemcpy(p->d_table, tab_bytes.data(), tab_bytes.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(p->d_h, h_bytes.data(), h_bytes.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemset(p->counters, 0, kNumCounters * sizeof(int))) != cudaSuccess) {
+      (e = cudaMemset(p->counters, 0, kNumCounters * sizeof(int))) != cudaSuccess ||
+      (p->model && (e = cudaMemset(p->model, 0, size_t(N) * size_t(N) * c2)) != cudaSuccess)) {
     free_plan(p);
     return cuda_error(e, "plan upload");
   }
@@ -600,8 +621,8 @@ int lmg_predict_vis(lmg_plan* p, const void* image, void* vis_out, void* stream)
   if (int rc = need_binned(p)) return rc;
   if (p->nvis > 0 && !vis_out) return set_error(LMG_EINVAL, "vis_out is NULL");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int rc = launch_status(pad_correct_launch(image, p->work, p->d_h, int(p->n_image), int(p->N), p->dtype, st), "pad");
-  if (rc == LMG_OK) rc = fft_model_pruned(p, p->work, st);
+  int rc = launch_status(pad_rows_launch(image, p->model, p->d_h, int(p->n_image), int(p->N), p->dtype, st), "pad");
+  if (rc == LMG_OK) rc = fft_model_to_work(p, st);
   if (rc == LMG_OK) rc = do_degrid(p, p->work, vis_out, st);
   return rc;
 }

@@ -51,7 +51,44 @@ __global__ void k_pad_correct(const typename Cplx<R>::T* __restrict__ img, typen
   P[static_cast<size_t>(iy) * N + ix] = o;
 }
 
+// The kept rows only of the padded, corrected model grid (row py of the image at grid row
+// qy mod N, every column of it); the other rows are left as they are (zero in the plan's
+// model buffer, which nothing else writes).
+template <typename R>
+__global__ void k_pad_rows(const typename Cplx<R>::T* __restrict__ img, typename Cplx<R>::T* __restrict__ P,
+                           const R* __restrict__ h, int n_img, int N) {
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+  const int py = blockIdx.y;
+  if (ix >= N) return;
+  const int half = n_img / 2;
+  const int qy = py - half, iy = qy < 0 ? qy + N : qy;
+  const int qx = ix < N / 2 ? ix : ix - N;
+  typename Cplx<R>::T o;
+  o.x = 0;
+  o.y = 0;
+  if (qx >= -half && qx < n_img - half) {
+    const int px = qx + half;
+    const auto v = img[static_cast<size_t>(py) * n_img + px];
+    R f = h[px] * h[py];
+    if ((qx + qy) & 1) f = -f;
+    o.x = f * v.x;
+    o.y = f * v.y;
+  }
+  P[static_cast<size_t>(iy) * N + ix] = o;
+}
+
 }  // namespace
+
+int pad_rows_launch(const void* img, void* P, const void* h, int n_img, int N, int dtype, cudaStream_t st) {
+  dim3 block(256), grid((N + 255) / 256, n_img);
+  if (dtype)
+    k_pad_rows<double><<<grid, block, 0, st>>>(static_cast<const double2*>(img), static_cast<double2*>(P),
+                                               static_cast<const double*>(h), n_img, N);
+  else
+    k_pad_rows<float><<<grid, block, 0, st>>>(static_cast<const float2*>(img), static_cast<float2*>(P),
+                                              static_cast<const float*>(h), n_img, N);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
 
 int crop_correct_launch(const void* F, void* img, const void* h, int n_img, int N, int dtype, cudaStream_t st) {
   dim3 block(256), grid((n_img + 255) / 256, n_img);

@@ -89,5 +89,7 @@ int sweep_config(int W, int dtype, int Ms, bool degrid, size_t limit, bool* tabl
 // Grid correction (Eqs. 4, 15) and its adjoint.
 int crop_correct_launch(const void* F, void* img, const void* h, int n_img, int N, int dtype, cudaStream_t st);
 int pad_correct_launch(const void* img, void* P, const void* h, int n_img, int N, int dtype, cudaStream_t st);
+// Pad + correct writing only the kept rows of P (the rest must already be zero).
+int pad_rows_launch(const void* img, void* P, const void* h, int n_img, int N, int dtype, cudaStream_t st);
 
 }  // namespace lmg

@@ -78,6 +78,7 @@ struct lmg_plan {
   int* counters = nullptr;
   void* spill = nullptr;
   void* work = nullptr;      // N x N work grid (null in batch channels)
+  void* model = nullptr;     // N x N model grid of lmg_predict_vis: zero outside the kept rows
   cufftHandle fft = 0;              // full 2-D transform (lmg_fft)
   bool fft_ok = false;
   // pruned transforms of lmg_dirty_image / lmg_predict_vis: 1-D batches over all rows,
