@@ -243,7 +243,7 @@ int plan_create(const lmg_table* t, int64_t n_image, double pixel_scale, int64_t
   p->max_vis = max_vis;
   p->n_strips = int(N / kStrip);
   const size_t rs = dtype == LMG_C128 ? 8 : 4;
-  p->Wp = dtype == LMG_C128 ? ((p->W + 1) & ~1) : ((p->W + 3) & ~3);
+  p->Wp = dtype == LMG_C128 ? ((p->W + 1) & ~1) : (p->W | 1);
   const int nblk = int((N + opt.min_rows_per_block - 1) / opt.min_rows_per_block);
   p->item_cap = p->n_strips * nblk + int((2 * max_vis) / opt.min_item_target) + 2;
   const long long L = (long long)p->n_strips * N;

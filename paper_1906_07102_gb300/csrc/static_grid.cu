@@ -29,7 +29,7 @@ constexpr int kMaxStrips = kMaxN / kStrip;
 constexpr long long kMaxBuckets = static_cast<long long>(kMaxStrips) * kMaxN;
 constexpr int kMaxItems = kMaxStrips * ((kMaxN + kRowsPerBlock - 1) / kRowsPerBlock) +
                           static_cast<int>((2 * kMaxVis) / kItemTarget) + 2;
-constexpr int kMaxWp = 16;      // float rows padded to a multiple of 4, W <= 16
+constexpr int kMaxWp = 17;      // float row stride W | 1 (odd), W <= 16
 constexpr int kMaxRing = 18;    // ring slots for W = 16
 
 constexpr size_t up256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -116,7 +116,7 @@ extern "C" int lmg_grid_static(const lmg_table* t, int64_t n_image, double pixel
   if (int rc = setup_device(dev, &s)) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   unsigned char* base = s->base;
-  const int W = t->W, Ms = t->Ms, Wp = (W + 3) & ~3;
+  const int W = t->W, Ms = t->Ms, Wp = W | 1;
 
   // Table rows in float32, padded to Wp, into the scratch.
   {

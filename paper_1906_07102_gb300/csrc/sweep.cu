@@ -28,7 +28,7 @@ int ring_slots(int W) { return kD * ((W + kD - 1 + kD - 1) / kD); }
 
 size_t sweep_smem_bytes(int W, int dtype, int Ms, bool table_in_smem, bool degrid, int warps) {
   const size_t rs = dtype ? 8 : 4;
-  const int Wp = dtype ? ((W + 1) & ~1) : ((W + 3) & ~3);
+  const int Wp = dtype ? ((W + 1) & ~1) : (W | 1);
   const size_t tab = table_in_smem ? align16(size_t(Ms + 1) * Wp * rs) : 0;
   return tab + size_t(warps) * stage_bytes(W, dtype, degrid);
 }
@@ -49,7 +49,7 @@ int sweep_occupancy(int W, int dtype, int accum, size_t smem_bytes, bool degrid,
 
 int sweep_config(int W, int dtype, int Ms, bool degrid, size_t limit, bool* table_in_smem, int* warps) {
   const size_t rs = dtype ? 8 : 4;
-  const int Wp = dtype ? ((W + 1) & ~1) : ((W + 3) & ~3);
+  const int Wp = dtype ? ((W + 1) & ~1) : (W | 1);
   *table_in_smem = align16(size_t(Ms + 1) * Wp * rs) <= 64 * 1024;
   for (int pass = 0; pass < 2; ++pass) {
     for (int w = kWarps; w >= 1; w >>= 1) {
