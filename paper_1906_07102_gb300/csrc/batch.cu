@@ -413,7 +413,7 @@ int fill_images(lmg_batch* b, int which, const void* const* src, void* const* ds
 }
 
 // Launch sequence of the sweeps of one operation: per W class, reset its work counter, the
-// persistent sweep, then the spill pass (gridding) or the fix-up (degridding).
+// persistent sweep (degridding: after zeroing the outputs), then the spill pass (gridding).
 int launch_sweeps(lmg_batch* b, int op, cudaStream_t s) {
   const bool degrid = op == kOpDegrid || op == kOpPredict;
   for (size_t i = 0; i < b->wcls.size(); ++i) {
@@ -434,7 +434,7 @@ int launch_sweeps(lmg_batch* b, int op, cudaStream_t s) {
     e = cudaLaunchKernel(batch_kernel_for(k.W, degrid), dim3(k.blocks[d]), dim3(32 * b->warps), params, k.smem[d], s);
     if (e != cudaSuccess) return cuda_error(e, "batch: sweep launch");
     if (!degrid) k_batch_spill<<<dim3(2 * b->sms, n), 256, 0, s>>>(k.d_desc[op]);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "batch: spill / fix-up launch");
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_error(e, "batch: spill / zeroing launch");
   }
   return LMG_OK;
 }
