@@ -281,7 +281,7 @@ struct lmg_batch {
   std::vector<void*> work;               // per channel work grid (inside its size class)
   lmg::BatchImg* d_img[2] = {nullptr, nullptr};  // crop (dirty image) and pad (predict)
   int* d_work = nullptr;                 // one work counter per W class
-  int rows_per_block = 256, item_target = 1024, warps = 8, tab_smem = 1;
+  int rows_per_block = 64, item_target = 512, warps = 8, tab_smem = 1;
   std::vector<const double*> uv;         // last binned uv sets (re-binned by the tuner)
   std::vector<int64_t> nvis;
   bool binned = false;
