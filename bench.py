@@ -373,13 +373,26 @@ def run_native(args):
     img_h = torch.empty(img_d.shape, dtype=img_d.dtype).pin_memory()
     pv_h = torch.empty(pv_d.shape, dtype=pv_d.dtype).pin_memory()
 
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+
     def e2e_step():
+        # copies overlap the library's work: visibilities and model go up while the
+        # positions are binned, the image comes down while the prediction runs; every
+        # dependency is a stream-order wait, so each step still reads its own inputs
         uv_d.copy_(uv_h, non_blocking=True)
-        vis_d.copy_(vis_h, non_blocking=True)
-        model_d.copy_(model_h, non_blocking=True)
-        step()
-        img_h.copy_(img_d, non_blocking=True)
+        s_in.wait_stream(stream)               # the previous step is done with vis / model
+        with torch.cuda.stream(s_in):
+            vis_d.copy_(vis_h, non_blocking=True)
+            model_d.copy_(model_h, non_blocking=True)
+        plan.bin(uv_d)
+        stream.wait_stream(s_in)
+        plan.dirty_image(vis_d, out=img_d)
+        s_out.wait_stream(stream)
+        with torch.cuda.stream(s_out):
+            img_h.copy_(img_d, non_blocking=True)
+        plan.predict_vis(model_d, out=pv_d)
         pv_h.copy_(pv_d, non_blocking=True)
+        stream.wait_stream(s_out)              # the image is on the host before the next step
 
     for _ in range(2):
         e2e_step()
