@@ -149,7 +149,8 @@ int lmg_plan_free(lmg_plan* p);
  * Eq. 6; sort into 32-column strips by support-start row; balanced work items). Must be
  * called before lmg_grid / lmg_degrid / lmg_dirty_image / lmg_predict_vis and again
  * whenever the positions change. uv: device float64 [nvis][2] in wavelengths,
- * 0 <= nvis <= max_vis. Allocates nothing. */
+ * 0 <= nvis <= max_vis; read by two kernels of this call (counting, then placing the
+ * records), so it must stay unchanged until the stream has run them. Allocates nothing. */
 int lmg_plan_bin(lmg_plan* p, const double* uv, int64_t nvis, void* stream);
 
 /* lmg_plan_dropped -- number of positions dropped by the last lmg_plan_bin (not finite
@@ -222,9 +223,9 @@ void* lmg_work_grid(lmg_plan* p);
  * a real-time pipeline that must not allocate while it runs. The paper has no
  * counterpart; this is a deployment variant of the existing path.
  *
- * All working memory (positions, records, bucket counts, work items, spill rows and the
+ * All working memory (bucket ranks, records, bucket counts, work items, spill rows and the
  * float32 copy of the table) lives in one fixed-size __device__ array of this library,
- * about 20 MB, which every GPU that loads the library holds until the process exits.
+ * about 16 MB, which every GPU that loads the library holds until the process exits.
  * Limits: nvis <= LMG_STATIC_MAX_VIS, grid N = n_image / x0 a multiple of 32 in
  * [64, LMG_STATIC_MAX_N], table oversample <= LMG_STATIC_MAX_OVERSAMPLE; larger sizes
  * return LMG_EINVAL with a message and do nothing.

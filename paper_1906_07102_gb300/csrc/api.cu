@@ -67,7 +67,7 @@ namespace lmg {
 
 void free_plan(lmg_plan* p) {
   if (!p) return;
-  void* ptrs[] = {p->d_table, p->d_h, p->pos, p->hist, p->offsets, p->rank, p->partial, p->recs,
+  void* ptrs[] = {p->d_table, p->d_h, p->hist, p->offsets, p->rank, p->partial, p->recs,
                   p->items, p->counters, p->spill, p->work, p->model};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -96,7 +96,6 @@ SweepArgs sweep_args(const lmg_plan* p) {
   a.W = p->W;
   a.dtype = p->dtype;
   a.item_cap = p->item_cap;
-  a.pos = p->pos;
   a.nvis = p->nvis;
   return a;
 }
@@ -294,7 +293,7 @@ int plan_create(const lmg_table* t, int64_t n_image, double pixel_scale, int64_t
   const size_t c2 = 2 * rs;
   if ((rc = dalloc(reinterpret_cast<unsigned char**>(&p->d_table), tab_bytes.size(), "table")) ||
       (rc = dalloc(reinterpret_cast<unsigned char**>(&p->d_h), h_bytes.size(), "correction")) ||
-      (rc = dalloc(&p->pos, size_t(max_vis), "positions")) || (rc = dalloc(&p->hist, size_t(L), "histogram")) ||
+      (rc = dalloc(&p->hist, size_t(L), "histogram")) ||
       (rc = dalloc(&p->offsets, size_t(L) + 1, "offsets")) || (rc = dalloc(&p->rank, size_t(max_vis), "ranks")) ||
       (rc = dalloc(&p->partial, size_t(p->nchunks), "scan")) || (rc = dalloc(&p->recs, size_t(2 * max_vis), "records")) ||
       (rc = dalloc(&p->items, size_t(p->item_cap), "items")) || (rc = dalloc(&p->counters, kNumCounters, "counters")) ||
@@ -377,7 +376,6 @@ int plan_bin(lmg_plan* p, const double* uv, int64_t nvis, cudaStream_t st) {
   a.item_target = p->item_target;
   a.item_cap = p->item_cap;
   a.max_blocks = p->sms * 8;
-  a.pos = p->pos;
   a.hist = p->hist;
   a.offsets = p->offsets;
   a.rank = p->rank;

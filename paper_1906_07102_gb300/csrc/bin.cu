@@ -6,9 +6,10 @@
 //                    rule, strip keys (one, or two when the support crosses into the next
 //                    strip); the bucket counter's returned value is the record's rank.
 //   2. scan          exclusive prefix sum of the bucket counts (strip-major, row-minor).
-//   3. k_bin_scatter records of each pair of rows (2m, 2m+1) of a strip -- the row group
-//                    the sweeps stage together -- to the pair's range, dealt so that any
-//                    32 consecutive records sample the whole pair (see dealt_position).
+//   3. k_bin_scatter positions recomputed from (u, v) (cheaper than storing and reloading
+//                    them), records of each pair of rows (2m, 2m+1) of a strip -- the row
+//                    group the sweeps stage together -- to the pair's range, dealt so that
+//                    any 32 consecutive records sample the whole pair (see dealt_position).
 //   4. k_make_items  per strip and block of rows: items holding about item_target records,
 //                    cut at even rows so that the sweeps' row groups are these pairs.
 #include <cuda_runtime.h>
@@ -19,6 +20,23 @@
 namespace lmg {
 namespace {
 
+// Support start (grid indices, wrapped to [0, N)) and table coordinates of position p =
+// (u, v); false for a dropped position (product not finite or |u| N pixel_scale >= 2^30).
+__device__ __forceinline__ bool vis_position(double2 p, double scale2, int W, int N, VisPos& vp) {
+  long long U, V;
+  if (!fixed_position(p.x, scale2, U) || !fixed_position(p.y, scale2, V)) return false;
+  long long n0, m0;
+  support_start(U, W, n0, vp.su);
+  support_start(V, W, m0, vp.sv);
+  long long xi = (n0 + N / 2) % N;
+  long long yi = (m0 + N / 2) % N;
+  if (xi < 0) xi += N;
+  if (yi < 0) yi += N;
+  vp.x0 = static_cast<int>(xi);
+  vp.y0 = static_cast<int>(yi);
+  return true;
+}
+
 // Pass 1: positions to grid cells (support rule), bucket keys, and each record's rank in
 // its bucket (the value returned by the bucket counter), so that pass 2 needs no atomics.
 // Each thread takes kCountIlp positions per iteration so that their bucket atomics are in
@@ -26,8 +44,8 @@ namespace {
 constexpr int kCountIlp = 4;
 
 __global__ void k_bin_count(const double* __restrict__ uv, long long nvis, double scale2, int W,
-                            int N, int n_strips, VisPos* __restrict__ pos, int2* __restrict__ rank,
-                            int* __restrict__ hist, int* __restrict__ counters) {
+                            int N, int n_strips, int2* __restrict__ rank, int* __restrict__ hist,
+                            int* __restrict__ counters) {
   const int lane = threadIdx.x & 31;  // for the dropped-position count
   const long long span = static_cast<long long>(blockDim.x) * kCountIlp;
   const long long stride = static_cast<long long>(gridDim.x) * span;
@@ -42,18 +60,7 @@ __global__ void k_bin_count(const double* __restrict__ uv, long long nvis, doubl
       bad[u] = false;
       vp[u] = VisPos{-1, 0, 0u, 0u};
       if (k < nvis) {
-        long long U, V;
-        const double2 p = reinterpret_cast<const double2*>(uv)[k];
-        if (fixed_position(p.x, scale2, U) && fixed_position(p.y, scale2, V)) {
-          long long n0, m0;
-          support_start(U, W, n0, vp[u].su);
-          support_start(V, W, m0, vp[u].sv);
-          long long xi = (n0 + N / 2) % N;
-          long long yi = (m0 + N / 2) % N;
-          if (xi < 0) xi += N;
-          if (yi < 0) yi += N;
-          vp[u].x0 = static_cast<int>(xi);
-          vp[u].y0 = static_cast<int>(yi);
+        if (vis_position(reinterpret_cast<const double2*>(uv)[k], scale2, W, N, vp[u])) {
           const int strip = vp[u].x0 / kStrip;
           key1[u] = strip * N + vp[u].y0;
           if ((vp[u].x0 % kStrip) + W > kStrip) key2[u] = ((strip + 1) % n_strips) * N + vp[u].y0;
@@ -71,10 +78,7 @@ __global__ void k_bin_count(const double* __restrict__ uv, long long nvis, doubl
 #pragma unroll
     for (int u = 0; u < kCountIlp; ++u) {
       const long long k = base + u * blockDim.x + threadIdx.x;
-      if (k < nvis) {
-        pos[k] = vp[u];
-        rank[k] = rk[u];
-      }
+      if (k < nvis) rank[k] = rk[u];
       const unsigned nb = __popc(__ballot_sync(0xffffffffu, bad[u]));
       if (lane == 0 && nb) atomicAdd(counters + kCntBad, static_cast<int>(nb));
     }
@@ -183,11 +187,13 @@ __device__ __forceinline__ int dealt_position(int rho, int n) {
   return j * q + min(j, r) + rho / nc;
 }
 
-__global__ void k_bin_scatter(const VisPos* __restrict__ pos, const int2* __restrict__ rank, long long nvis,
-                              int W, int N, int n_strips, const int* __restrict__ offsets,
+__global__ void k_bin_scatter(const double* __restrict__ uv, double scale2, const int2* __restrict__ rank,
+                              long long nvis, int W, int N, int n_strips, const int* __restrict__ offsets,
                               Rec* __restrict__ recs) {
   // kCountIlp visibilities per thread per iteration: their position, rank and offset loads
-  // are in flight together (the pass is bound by the latency of these dependent loads)
+  // are in flight together (the pass is bound by the latency of these dependent loads).
+  // (u, v) and the ranks are read for the last time here: streaming loads (evict first)
+  // leave the L2 to the offsets and the records being written.
   const long long span = static_cast<long long>(blockDim.x) * kCountIlp;
   const long long stride = static_cast<long long>(gridDim.x) * span;
   for (long long base = static_cast<long long>(blockIdx.x) * span; base < nvis; base += stride) {
@@ -199,8 +205,8 @@ __global__ void k_bin_scatter(const VisPos* __restrict__ pos, const int2* __rest
       vp[u] = VisPos{-1, 0, 0u, 0u};
       rk[u] = make_int2(0, 0);
       if (k < nvis) {
-        vp[u] = pos[k];
-        rk[u] = rank[k];
+        rk[u] = __ldcs(rank + k);
+        vis_position(__ldcs(reinterpret_cast<const double2*>(uv) + k), scale2, W, N, vp[u]);
       }
     }
     int g1[kCountIlp], g2[kCountIlp];  // bucket pair bases (-1: none)
@@ -289,13 +295,14 @@ int bin_launch(const BinArgs& a, cudaStream_t st) {
   const int threads = 256;
   const long long want_c = (a.nvis + threads * kCountIlp - 1) / (threads * kCountIlp);
   const int blocks_c = static_cast<int>(want_c < a.max_blocks ? (want_c > 0 ? want_c : 1) : a.max_blocks);
-  k_bin_count<<<blocks_c, threads, 0, st>>>(a.uv, a.nvis, a.scale2, a.W, a.N, a.n_strips, a.pos, a.rank, a.hist,
+  k_bin_count<<<blocks_c, threads, 0, st>>>(a.uv, a.nvis, a.scale2, a.W, a.N, a.n_strips, a.rank, a.hist,
                                           a.counters);
   const int nchunks = static_cast<int>((L + kScanChunk - 1) / kScanChunk);
   k_scan_partials<<<nchunks, kScanThreads, 0, st>>>(a.hist, L, a.partial);
   k_scan_top<<<1, 1024, 0, st>>>(a.partial, nchunks);
   k_scan_final<<<nchunks, kScanThreads, 0, st>>>(a.hist, L, a.partial, a.offsets);
-  k_bin_scatter<<<blocks_c, threads, 0, st>>>(a.pos, a.rank, a.nvis, a.W, a.N, a.n_strips, a.offsets, a.recs);
+  k_bin_scatter<<<blocks_c, threads, 0, st>>>(a.uv, a.scale2, a.rank, a.nvis, a.W, a.N, a.n_strips, a.offsets,
+                                            a.recs);
   const int nblk = (a.N + a.rows_per_block - 1) / a.rows_per_block;
   const int ntask = a.n_strips * nblk;
   if (a.rows_per_block > kMaxRowsPerBlock) return -1;

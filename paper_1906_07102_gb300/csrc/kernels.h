@@ -9,7 +9,6 @@ namespace lmg {
 // Nodes k = 0..Ng of the direct calculation's folded sums (Ng = 32, Appendix A).
 constexpr int kDirectNodes = 33;
 
-struct VisPos;
 struct Rec;
 struct Item;
 
@@ -31,7 +30,6 @@ struct BinArgs {
   int W, N, n_strips;
   int rows_per_block, item_target, item_cap;
   int max_blocks;
-  VisPos* pos;
   int* hist;       // n_strips * N
   int* offsets;    // n_strips * N + 1
   int2* rank;      // max_vis: rank of the record(s) in their buckets
@@ -67,7 +65,6 @@ struct SweepArgs {
   // degridding
   const void* grid_in;
   void* vis_out;
-  const VisPos* pos;  // per visibility support start (x0 < 0: dropped)
   long long nvis;
 };
 

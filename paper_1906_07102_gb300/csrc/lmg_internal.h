@@ -70,7 +70,6 @@ struct lmg_plan {
   int blocks_grid_comp = 0;
   void* d_table = nullptr;
   void* d_h = nullptr;
-  lmg::VisPos* pos = nullptr;
   int* hist = nullptr;
   int* offsets = nullptr;
   int2* rank = nullptr;

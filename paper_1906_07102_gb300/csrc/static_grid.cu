@@ -36,8 +36,7 @@ constexpr size_t up256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // Byte offsets of the buffers inside the scratch array (sized for the maxima above).
 constexpr size_t kOffTable = 0;
-constexpr size_t kOffPos = kOffTable + up256(sizeof(float) * (kMaxOversample + 1) * kMaxWp);
-constexpr size_t kOffRank = kOffPos + up256(sizeof(VisPos) * kMaxVis);
+constexpr size_t kOffRank = kOffTable + up256(sizeof(float) * (kMaxOversample + 1) * kMaxWp);
 constexpr size_t kOffHist = kOffRank + up256(sizeof(int2) * kMaxVis);
 constexpr size_t kOffOffsets = kOffHist + up256(sizeof(int) * kMaxBuckets);
 constexpr size_t kOffPartial = kOffOffsets + up256(sizeof(int) * (kMaxBuckets + 1));
@@ -142,7 +141,6 @@ extern "C" int lmg_grid_static(const lmg_table* t, int64_t n_image, double pixel
   b.item_target = kItemTarget;
   b.item_cap = item_cap;
   b.max_blocks = s->sms * 8;
-  b.pos = reinterpret_cast<VisPos*>(base + kOffPos);
   b.rank = reinterpret_cast<int2*>(base + kOffRank);
   b.hist = reinterpret_cast<int*>(base + kOffHist);
   b.offsets = reinterpret_cast<int*>(base + kOffOffsets);
