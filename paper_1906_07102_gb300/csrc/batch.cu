@@ -145,11 +145,10 @@ __global__ void k_batch_spill(const BatchChan* __restrict__ ch) {
   int nfront;
   const int total = work_total(a.counters, a.item_cap, nfront);
   const int RS = ring_slots_dev(a.W);
-  const long long gw = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  const long long n = static_cast<long long>(total) * RS;
-  for (long long w = gw; w < n; w += (static_cast<long long>(gridDim.x) * blockDim.x) >> 5)
-    spill_unit<float>(a.items, nfront, a.item_cap, a.W, RS, a.N, static_cast<const float2*>(a.spill),
+  for (int w = gw; w < total; w += (gridDim.x * blockDim.x) >> 5)
+    spill_item<float>(a.items, nfront, a.item_cap, a.W, RS, a.N, static_cast<const float2*>(a.spill),
                       static_cast<float2*>(a.grid), w, lane);
 }
 
@@ -167,37 +166,41 @@ __global__ void k_batch_zero(const BatchChan* __restrict__ ch) {
 // single-plan correction (checkerboard for the centring shift).
 __global__ void k_batch_crop(const BatchImg* __restrict__ im) {
   const BatchImg d = im[blockIdx.y];
-  const long long n = static_cast<long long>(d.n_img) * d.n_img;
-  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
-  for (long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += stride) {
-    const int py = static_cast<int>(k / d.n_img), px = static_cast<int>(k % d.n_img);
-    const int qx = px - d.n_img / 2, qy = py - d.n_img / 2;
-    const int sx = qx < 0 ? qx + d.N : qx, sy = qy < 0 ? qy + d.N : qy;
-    const float2 v = d.src[static_cast<size_t>(sy) * d.N + sx];
-    float f = d.h[px] * d.h[py];
-    if ((qx + qy) & 1) f = -f;
-    d.dst[k] = make_float2(f * v.x, f * v.y);
+  for (int py = blockIdx.x; py < d.n_img; py += gridDim.x) {
+    const int qy = py - d.n_img / 2, sy = qy < 0 ? qy + d.N : qy;
+    const float2* src = d.src + static_cast<size_t>(sy) * d.N;
+    float2* dst = d.dst + static_cast<size_t>(py) * d.n_img;
+    for (int px = threadIdx.x; px < d.n_img; px += blockDim.x) {
+      const int qx = px - d.n_img / 2, sx = qx < 0 ? qx + d.N : qx;
+      const float2 v = src[sx];
+      float f = d.h[px] * d.h[py];
+      if ((qx + qy) & 1) f = -f;
+      dst[px] = make_float2(f * v.x, f * v.y);
+    }
   }
 }
 
-// Pad + correct of every channel (blockIdx.y = channel).
+// Pad + correct of every channel (blockIdx.y = channel), one grid row per block iteration.
 __global__ void k_batch_pad(const BatchImg* __restrict__ im) {
   const BatchImg d = im[blockIdx.y];
-  const long long n = static_cast<long long>(d.N) * d.N;
-  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
   const int half = d.n_img / 2;
-  for (long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += stride) {
-    const int iy = static_cast<int>(k / d.N), ix = static_cast<int>(k % d.N);
-    const int qx = ix < d.N / 2 ? ix : ix - d.N, qy = iy < d.N / 2 ? iy : iy - d.N;
-    float2 o = make_float2(0.f, 0.f);
-    if (qx >= -half && qx < d.n_img - half && qy >= -half && qy < d.n_img - half) {
-      const int px = qx + half, py = qy + half;
-      const float2 v = d.src[static_cast<size_t>(py) * d.n_img + px];
-      float f = d.h[px] * d.h[py];
-      if ((qx + qy) & 1) f = -f;
-      o = make_float2(f * v.x, f * v.y);
+  for (int iy = blockIdx.x; iy < d.N; iy += gridDim.x) {
+    const int qy = iy < d.N / 2 ? iy : iy - d.N;
+    const bool kept_row = qy >= -half && qy < d.n_img - half;
+    const int py = qy + half;
+    float2* dst = d.dst + static_cast<size_t>(iy) * d.N;
+    for (int ix = threadIdx.x; ix < d.N; ix += blockDim.x) {
+      const int qx = ix < d.N / 2 ? ix : ix - d.N;
+      float2 o = make_float2(0.f, 0.f);
+      if (kept_row && qx >= -half && qx < d.n_img - half) {
+        const int px = qx + half;
+        const float2 v = d.src[static_cast<size_t>(py) * d.n_img + px];
+        float f = d.h[px] * d.h[py];
+        if ((qx + qy) & 1) f = -f;
+        o = make_float2(f * v.x, f * v.y);
+      }
+      dst[ix] = o;
     }
-    d.dst[k] = o;
   }
 }
 

@@ -9,13 +9,11 @@ template <typename R>
 __global__ void k_grid_spill(const Item* __restrict__ items, const int* __restrict__ counters, int item_cap,
                              int W, int RS, int N, const typename Cplx<R>::T* __restrict__ spill,
                              typename Cplx<R>::T* __restrict__ grid) {
+  // one warp per item slot (the launch covers item_cap slots)
   int nfront;
   const int total = work_total(counters, item_cap, nfront);
-  const long long gw = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  const long long n = static_cast<long long>(total) * RS;
-  for (long long w = gw; w < n; w += (static_cast<long long>(gridDim.x) * blockDim.x) >> 5)
-    spill_unit<R>(items, nfront, item_cap, W, RS, N, spill, grid, w, lane);
+  const int w = static_cast<int>((static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
+  if (w < total) spill_item<R>(items, nfront, item_cap, W, RS, N, spill, grid, w, threadIdx.x & 31);
 }
 
 void* kernel_for(int W, int dtype, int accum, bool degrid, bool ext) {
@@ -71,7 +69,7 @@ int grid_launch(const SweepArgs& a, cudaStream_t st) {
   SweepArgs args = a;
   void* params[] = {&args};
   if (cudaLaunchKernel(k, dim3(a.grid_blocks), dim3(32 * a.warps), params, smem, st) != cudaSuccess) return -1;
-  const int spill_blocks = 2 * 152;
+  const int spill_blocks = (a.item_cap + 7) / 8;  // 8 warps of 256 threads, one per item slot
   if (a.dtype) {
     k_grid_spill<double><<<spill_blocks, 256, 0, st>>>(a.items, a.counters, a.item_cap, a.W, ring_slots(a.W), a.N,
                                                        static_cast<const double2*>(a.spill),

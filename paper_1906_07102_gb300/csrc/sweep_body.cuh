@@ -451,22 +451,28 @@ __device__ __forceinline__ void grid_item(const SweepArgs& a, const R* __restric
   }
 }
 
-// Spill unit w (item w / RS, ring slot w % RS): adds the slot's row into the grid when the
-// slot holds one of the W - 1 rows past its item (after every item stored its own rows).
+// Spill rows of work item w, run by the 32 lanes of a warp after every item stored its own
+// rows: the W - 1 rows past the item (relative rows nrows + j, j < W - 1, held in ring slot
+// (nrows + j) mod RS) are added into the grid. All of them are loaded before the first
+// add, so that the warp waits for one round of loads.
 template <typename R>
-__device__ __forceinline__ void spill_unit(const Item* __restrict__ items, int nfront, int item_cap, int W, int RS,
+__device__ __forceinline__ void spill_item(const Item* __restrict__ items, int nfront, int item_cap, int W, int RS,
                                            int N, const typename Cplx<R>::T* __restrict__ spill,
-                                           typename Cplx<R>::T* __restrict__ grid, long long w, int lane) {
-  const int slot = item_slot(static_cast<int>(w / RS), nfront, item_cap);
-  const int q = static_cast<int>(w % RS);
+                                           typename Cplx<R>::T* __restrict__ grid, int w, int lane) {
+  constexpr int kMaxRows = 15;  // W - 1 for W <= 16
+  const int slot = item_slot(w, nfront, item_cap);
   const Item item = items[slot];
   const int nrows = item.r1 - item.r0;
   if (nrows <= 0 || item.nrec == 0) return;
-  const int j = ((q - nrows) % RS + RS) % RS;
-  if (j > W - 2) return;
-  const int row = (item.r1 + j) % N;
-  const auto v = spill[(static_cast<size_t>(slot) * RS + q) * kStrip + lane];
-  red_add(grid + static_cast<size_t>(row) * N + item.strip * kStrip + lane, v);
+  const typename Cplx<R>::T* sp = spill + static_cast<size_t>(slot) * RS * kStrip + lane;
+  typename Cplx<R>::T v[kMaxRows];
+#pragma unroll
+  for (int j = 0; j < kMaxRows; ++j)
+    if (j < W - 1) v[j] = sp[((nrows + j) % RS) * kStrip];
+  typename Cplx<R>::T* g = grid + item.strip * kStrip + lane;
+#pragma unroll
+  for (int j = 0; j < kMaxRows; ++j)
+    if (j < W - 1) red_add(g + static_cast<size_t>((item.r1 + j) % N) * N, v[j]);
 }
 
 // One degridding work item, run by the 32 lanes of a warp (see grid_item).

@@ -189,6 +189,33 @@ def test_fp32_fft_and_correction_stages(c2):
     assert rel_rms(img, ref_img) < 1e-5
 
 
+def _offset_view(x, shape):
+    """Copy of x in a buffer one element past a 16-byte boundary (8-byte aligned)."""
+    n = int(np.prod(shape))
+    buf = torch.empty(n + 1, dtype=x.dtype, device=x.device)
+    v = buf[1:].view(*shape)
+    v.copy_(x.reshape(shape))
+    return v
+
+
+def test_correction_pair_and_scalar_kernels_agree(c2):
+    """Crop, pad and the prediction's kept-row pad on 16-byte aligned complex64 arrays take
+    the two-pixel kernels; arrays offset by one element take the one-pixel kernels. Both
+    give the same bits."""
+    uv, dl, vis, p, T, hv, op = c2
+    F = to_dev(S.random_image(N2, 21).astype(np.complex64), torch.complex64)
+    img_pair = p.crop_correct(F)
+    img_one = p.crop_correct(_offset_view(F, (N2, N2)), out=_offset_view(torch.zeros_like(img_pair), (n2, n2)))
+    assert img_one.data_ptr() % 16 == 8 and torch.equal(img_pair, img_one)
+    M = to_dev(S.random_image(n2, 22).astype(np.complex64), torch.complex64)
+    pad_pair = p.pad_correct(M)
+    pad_one = p.pad_correct(_offset_view(M, (n2, n2)), out=_offset_view(torch.zeros_like(pad_pair), (N2, N2)))
+    assert torch.equal(pad_pair, pad_one)
+    pv_pair = p.predict_vis(M)
+    pv_one = p.predict_vis(_offset_view(M, (n2, n2)))
+    assert torch.equal(pv_pair, pv_one)
+
+
 def test_pruned_ffts_match_full_fft_on_the_kept_field(c2):
     """lmg_fft_pruned: equal to the full transform at the kept rows and columns (imaging),
     and on a padded model grid (prediction)."""
