@@ -167,12 +167,27 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------------------
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi sampling during the timed region: start() waits for the sampler's first
+    line, mark() notes where the timed region begins, stop() keeps the samples taken from
+    there on (at least one, waiting briefly for it when the region was shorter than the
+    sampling interval)."""
 
     def __init__(self, index):
         self.proc = None
         self.index = index
         self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.first = 0
+
+    def _lines(self):
+        with open(self.path) as f:
+            return [ln for ln in f.read().splitlines() if ln.count(",") >= 8]
+
+    def _wait_lines(self, n, timeout):
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < timeout:
+            if len(self._lines()) >= n:
+                return
+            time.sleep(0.01)
 
     def start(self):
         try:
@@ -184,12 +199,18 @@ class Clocks:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
+            self._wait_lines(1, 2.0)
         except (OSError, FileNotFoundError):
             self.proc = None
+
+    def mark(self):
+        if self.proc is not None:
+            self.first = len(self._lines())
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self._wait_lines(self.first + 1, 1.0)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -198,19 +219,16 @@ class Clocks:
         self.f.close()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        with open(self.path) as f:
-            for line in f:
-                parts = [p.strip() for p in line.split(",")]
-                if len(parts) < 9:
-                    continue
-                try:
-                    sm.append(float(parts[1]))
-                    smax.append(float(parts[2]))
-                except ValueError:
-                    continue
-                for nm, v in zip(names, parts[5:9]):
-                    if v.lower().startswith("active"):
-                        reasons.add(nm)
+        for line in self._lines()[self.first:]:
+            parts = [p.strip() for p in line.split(",")]
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(np.max(smax)), "reasons": sorted(reasons),
@@ -321,10 +339,11 @@ def run_native(args):
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     clocks = Clocks(local)
+    clocks.start()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    clocks.mark()
     t_wall = time.perf_counter()
     for k in range(args.steps):
         flush.zero_()
@@ -366,42 +385,68 @@ def run_native(args):
     timed("dirty_image", lambda: plan.dirty_image(vis_d, out=img_d))
     timed("predict_vis", lambda: plan.predict_vis(model_d, out=pv_d))
 
-    # end to end through the public API with pinned host buffers
+    # end to end through the public API with pinned host buffers: every step uploads its
+    # uv, visibilities and model and downloads its image and predictions. Two sets of device
+    # buffers let step k+1's uploads and step k's downloads run on copy streams while step k
+    # computes; every reuse of a buffer waits (stream-order events) for the work that last
+    # used it, so each step reads its own inputs.
     uv_h = torch.from_numpy(uv).pin_memory()
     vis_h = torch.from_numpy(vis).pin_memory()
     model_h = torch.from_numpy(model).pin_memory()
     img_h = torch.empty(img_d.shape, dtype=img_d.dtype).pin_memory()
     pv_h = torch.empty(pv_d.shape, dtype=pv_d.dtype).pin_memory()
-
+    bufs = [dict(uv=uv_d, vis=vis_d, model=model_d, img=img_d, pv=pv_d),
+            dict(uv=torch.empty_like(uv_d), vis=torch.empty_like(vis_d), model=torch.empty_like(model_d),
+                 img=torch.empty_like(img_d), pv=torch.empty_like(pv_d))]
     s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
 
-    def e2e_step():
-        # copies overlap the library's work: visibilities and model go up while the
-        # positions are binned, the image comes down while the prediction runs; every
-        # dependency is a stream-order wait, so each step still reads its own inputs
-        uv_d.copy_(uv_h, non_blocking=True)
-        s_in.wait_stream(stream)               # the previous step is done with vis / model
-        with torch.cuda.stream(s_in):
-            vis_d.copy_(vis_h, non_blocking=True)
-            model_d.copy_(model_h, non_blocking=True)
-        plan.bin(uv_d)
-        stream.wait_stream(s_in)
-        plan.dirty_image(vis_d, out=img_d)
-        s_out.wait_stream(stream)
-        with torch.cuda.stream(s_out):
-            img_h.copy_(img_d, non_blocking=True)
-        plan.predict_vis(model_d, out=pv_d)
-        pv_h.copy_(pv_d, non_blocking=True)
-        stream.wait_stream(s_out)              # the image is on the host before the next step
+    def ev():
+        return torch.cuda.Event()
 
-    for _ in range(2):
-        e2e_step()
+    def e2e_run(k_steps):
+        up = [ev(), ev()]          # inputs of the set uploaded
+        used = [ev(), ev()]        # compute done with the set's inputs and outputs
+        down = [ev(), ev()]        # outputs of the set downloaded
+        for e in used + down:
+            e.record(stream)
+
+        def upload(b):
+            s_in.wait_event(used[b])
+            with torch.cuda.stream(s_in):
+                bufs[b]["uv"].copy_(uv_h, non_blocking=True)
+                bufs[b]["vis"].copy_(vis_h, non_blocking=True)
+                bufs[b]["model"].copy_(model_h, non_blocking=True)
+                up[b].record(s_in)
+
+        upload(0)
+        for k in range(k_steps):
+            b = k % 2
+            if k + 1 < k_steps:
+                upload(1 - b)
+            stream.wait_event(up[b])
+            stream.wait_event(down[b])
+            d = bufs[b]
+            plan.bin(d["uv"])
+            plan.dirty_image(d["vis"], out=d["img"])
+            img_ready = ev()
+            img_ready.record(stream)
+            plan.predict_vis(d["model"], out=d["pv"])
+            used[b].record(stream)
+            s_out.wait_event(img_ready)
+            with torch.cuda.stream(s_out):
+                img_h.copy_(d["img"], non_blocking=True)
+                s_out.wait_event(used[b])
+                pv_h.copy_(d["pv"], non_blocking=True)
+                down[b].record(s_out)
+        stream.wait_stream(s_out)              # the last results are on the host
+        stream.wait_stream(s_in)
+
+    e2e_run(2)
     torch.cuda.synchronize()
     es, ee = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ek = max(3, min(args.steps, 10))
     es.record(stream)
-    for _ in range(ek):
-        e2e_step()
+    e2e_run(ek)
     ee.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(es.elapsed_time(ee) / ek, dev)
@@ -418,6 +463,7 @@ def run_native(args):
     degrid_bytes = grid_bytes
     extra = {"stages_ms": stages,
              "grid_degrid_mvis_s": nv / ((stages["grid"] + stages["degrid"]) * 1e-3) / 1e6,
+             "bin_grid_degrid_mvis_s": nv / ((stages["bin"] + stages["grid"] + stages["degrid"]) * 1e-3) / 1e6,
              "degrid_roofline_frac": degrid_bytes / (stages["degrid"] * 1e-3) / 1e9 / peak,
              "timed_wall_s": t_wall}
 
@@ -535,6 +581,7 @@ def run_channels(args):
     torch.cuda.synchronize()
     clocks = Clocks(0)
     clocks.start()
+    clocks.mark()
     t_wall = time.perf_counter()
     ms_b = _events_ms(batched, args.steps, flush, stream, torch)
     t_wall = time.perf_counter() - t_wall
@@ -648,6 +695,7 @@ def run_autograd(args):
     torch.cuda.synchronize()
     clocks = Clocks(0)
     clocks.start()
+    clocks.mark()
     ms_b = _events_ms(batched, args.steps, flush, stream, torch)
     clk = clocks.stop()
     ms_p = _events_ms(per_channel, args.steps, flush, stream, torch)
@@ -732,6 +780,7 @@ def run_large(args):
     steps = max(3, min(args.steps, 10))
     clocks = Clocks(0)
     clocks.start()
+    clocks.mark()
     ms_plain = _events_ms(lambda: p32.grid(v64, out=grid), steps, flush, stream, torch)
     ms_comp = _events_ms(lambda: p32.grid(v64, accum="compensated", out=grid), steps, flush, stream, torch)
     ms_degrid = _events_ms(lambda: p32.degrid(grid, out=out), steps, flush, stream, torch)
