@@ -25,9 +25,9 @@
 //      The W-1 rows past the item go to a spill buffer and are added by k_grid_spill once
 //      all items have stored their rows.
 //      degridding: the ring holds grid rows of the lane's column; lane t forms
-//      Cu_i sum_q Cv'_q G[row0 + q][t] for each covering record and stages it; lane l sums
-//      its record's partial sums and adds the result to the zeroed output (a visibility
-//      whose support crosses a strip has two records, one per strip).
+//      sum_q Cv'_q G[row0 + q][t] for each covering record and stages it; lane l sums
+//      Cu_i times its record's W staged sums and adds the result to the zeroed output (a
+//      visibility whose support crosses a strip has two records, one per strip).
 // Every grid cell is written exactly once by the gridding sweep (no pre-zeroing, no
 #pragma once
 
@@ -561,15 +561,8 @@ __device__ __forceinline__ void degrid_item(const SweepArgs& a, const R* __restr
                 s1 = f2fma(f2pack(c1, c1), g2[(gp * kD + q) % RS], s1);
                 s2 = f2fma(f2pack(c2, c2), g2[(gp * kD + q) % RS], s2);
               }
-              const float2 f1 = f2unpack(s1), f2 = f2unpack(s2);
-              const R cu1 = s_cu[l1 * W + i1], cu2 = s_cu[l2 * W + i2];
-              C2 p1, p2;
-              p1.x = cu1 * f1.x;
-              p1.y = cu1 * f1.y;
-              p2.x = cu2 * f2.x;
-              p2.y = cu2 * f2.y;
-              s_p[l1 * W + i1] = p1;
-              if (two) s_p[l2 * W + i2] = p2;
+              s_p[l1 * W + i1] = f2unpack(s1);
+              if (two) s_p[l2 * W + i2] = f2unpack(s2);
             }
           }
           while (M) {
@@ -595,20 +588,22 @@ __device__ __forceinline__ void degrid_item(const SweepArgs& a, const R* __restr
                 si = fma(c, g_im[(gp * kD + q) % RS], si);
               }
             }
-            const R cu_i = s_cu[l * W + i];
             C2 p;
-            p.x = cu_i * sr;
-            p.y = cu_i * si;
+            p.x = sr;
+            p.y = si;
             s_p[l * W + i] = p;
           }
           __syncwarp();
           if (mine) {
             const int i0 = max(0, -xrel), i1 = min(W, kStrip - xrel);
             R vr = R(0), vi = R(0);
-            for (int ii = i0; ii < i1; ++ii) {
+#pragma unroll
+            for (int ii = 0; ii < W; ++ii) {
+              if (ii < i0 || ii >= i1) continue;
               const C2 p = s_p[lane * W + ii];
-              vr += p.x;
-              vi += p.y;
+              const R c = s_cu[lane * W + ii];
+              vr = fma(c, p.x, vr);
+              vi = fma(c, p.y, vi);
             }
             C2 o;
             o.x = vr;
