@@ -202,6 +202,8 @@ class Clocks:
             self._wait_lines(1, 2.0)
         except (OSError, FileNotFoundError):
             self.proc = None
+            if getattr(self, "f", None) is not None:
+                self.f.close()
 
     def mark(self):
         if self.proc is not None:
