@@ -271,7 +271,9 @@ int lmg_batch_create(int n_chan, const lmg_table* const* tables, const int64_t* 
 int lmg_batch_free(lmg_batch* b);
 
 /* lmg_batch_bin -- bins channel c's uv[c] (device float64 [nvis[c]][2], 16-byte aligned)
- * for every c; uv[c] may be NULL when nvis[c] == 0. Invalidates captured graphs. */
+ * for every c; uv[c] may be NULL when nvis[c] == 0. As for lmg_plan_bin, each uv[c] is
+ * read by two kernels on the stream and must stay unchanged until the stream has run
+ * them. Invalidates captured graphs. */
 int lmg_batch_bin(lmg_batch* b, const double* const* uv, const int64_t* nvis, void* stream);
 
 /* lmg_batch_grid -- grid[c] = gridded vis[c] (x weights[c]) for every channel, as lmg_grid
