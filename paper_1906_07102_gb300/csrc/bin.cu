@@ -191,7 +191,7 @@ __global__ void k_bin_scatter(const double* __restrict__ uv, double scale2, cons
                               long long nvis, int W, int N, int n_strips, const int* __restrict__ offsets,
                               Rec* __restrict__ recs) {
   // kCountIlp visibilities per thread per iteration: their position, rank and offset loads
-  // are in flight together (the pass is bound by the latency of these dependent loads).
+  // are in flight together (the pass is bound by its random L2 requests and their latency).
   // (u, v) and the ranks are read for the last time here: streaming loads (evict first)
   // leave the L2 to the offsets and the records being written.
   const long long span = static_cast<long long>(blockDim.x) * kCountIlp;
