@@ -53,7 +53,9 @@ def support_rule(u_cells, W):
 
 
 def s_float32(S):
-    """Table coordinate rounded once to float32, as the single-precision path stores it."""
+    """Table coordinate rounded once to float32. Diagnostic only (``Plan(...,
+    single_precision_s=True)``): it shows how much one float32 rounding of s moves a
+    result; every parity reference uses the exact float64 coordinate."""
     return (np.asarray(S, dtype=np.float64) * 2.0 ** -FRAC_BITS).astype(np.float32)
 
 
@@ -63,9 +65,13 @@ def s_float64(S):
 
 
 class Plan:
-    """Support starts and table coordinates for a set of (u, v) cell positions."""
+    """Support starts and table coordinates for a set of (u, v) cell positions.
 
-    def __init__(self, u_cells, v_cells, W, N, single_precision_s=True):
+    The coordinates are exact float64 values of s (the default, used by every parity
+    reference). ``single_precision_s=True`` is a named diagnostic that rounds s to float32
+    and takes the nearest-row decision in float32."""
+
+    def __init__(self, u_cells, v_cells, W, N, single_precision_s=False):
         self.W, self.N = W, N
         self.n0, Su, vu = support_rule(u_cells, W)
         self.m0, Sv, vv = support_rule(v_cells, W)

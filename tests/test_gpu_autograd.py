@@ -101,7 +101,7 @@ def test_gradient_matches_fp64_oracle(small):
     T = oracle_table(W, 0.5, MS)
     hv = oracle_hvec(T, MS, "linear", W, n_S, N_S)
     uc = I.cells_from_wavelengths(uv, N_S, dl)
-    op = I.Plan(uc[:, 0], uc[:, 1], W, N_S, single_precision_s=True)
+    op = I.Plan(uc[:, 0], uc[:, 1], W, N_S, single_precision_s=False)
     r = I.predict_vis(op, T, MS, 1, hv, image.astype(np.complex128)) - vis.astype(np.complex64)
     g_ref = 2.0 * I.dirty_image(op, T, MS, 1, hv, n_S, r).real
     L_ref = float(np.sum(np.abs(r) ** 2))
@@ -185,6 +185,6 @@ def test_full_size_forward_on_sampled_visibilities(full):
     T = oracle_table(W, 0.5, MS)
     hv = oracle_hvec(T, MS, "linear", W, n_F, N_F)
     uc = I.cells_from_wavelengths(uv[k], N_F, dl)
-    op = I.Plan(uc[:, 0], uc[:, 1], W, N_F, single_precision_s=True)
+    op = I.Plan(uc[:, 0], uc[:, 1], W, N_F, single_precision_s=False)
     ref = I.predict_vis(op, T, MS, 1, hv, img.cpu().numpy().astype(np.complex128))
     assert rel_rms(PI[k], ref) < 1e-5

@@ -107,7 +107,7 @@ def test_batch_channel_against_oracle(setup):
     T = oracle_table(W, 0.5, MS)
     hv = oracle_hvec(T, MS, "linear", W, N // 2, N)
     uc = I.cells_from_wavelengths(uvs[c].cpu().numpy(), N, 1.0 / N)
-    op = I.Plan(uc[:, 0], uc[:, 1], W, N, single_precision_s=True)
+    op = I.Plan(uc[:, 0], uc[:, 1], W, N, single_precision_s=False)
     ref = I.dirty_image(op, T, MS, 1, hv, N // 2, viss[c].cpu().numpy().astype(np.complex128))
     assert rel_rms(img, ref) < 1e-5
 

@@ -131,7 +131,7 @@ def c2():
     p.bin(to_dev(uv, torch.float64))
     T = oracle_table(W2, 0.5, M2)
     hv = oracle_hvec(T, M2, "linear", W2, n2, N2)
-    op = oracle_plan(uv, dl, W2, N2, single=True)
+    op = oracle_plan(uv, dl, W2, N2, single=False)
     return uv, dl, vis64, p, T, hv, op
 
 
@@ -415,7 +415,7 @@ def test_compensated_accumulation_not_worse():
     vd = to_dev(vis, torch.complex64)
     plain = p.grid(vd).cpu().numpy()
     comp = p.grid(vd, accum="compensated").cpu().numpy()
-    ref = I.grid(oracle_plan(uv, 1.0 / N, W, N, single=True), T, Ms, 1, vis.astype(np.complex64).astype(np.complex128))
+    ref = I.grid(oracle_plan(uv, 1.0 / N, W, N, single=False), T, Ms, 1, vis.astype(np.complex64).astype(np.complex128))
     e_plain, e_comp = rel_rms(plain, ref), rel_rms(comp, ref)
     assert e_comp <= e_plain * 1.01
     assert e_comp < 1e-6

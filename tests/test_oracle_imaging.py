@@ -197,3 +197,34 @@ def test_dirty_pixels_direct_matches_fft_path():
     py, px = np.array([0, 5, 16, 31]), np.array([3, 16, 0, 31])
     d = I.dirty_pixels_direct(plan, T, Ms, 1, hvec[px], hvec[py], vis, None, x[px], x[py])
     np.testing.assert_allclose(d, img[py, px], atol=1e-12 * np.abs(img).max())
+
+
+@pytest.mark.parametrize("W,interp,Ms", [(3, 0, 100), (7, 1, 1000)])
+def test_bounds_are_equalities_for_one_term(W, interp, Ms):
+    """The per-pixel bound of Eq. 8 comes from one Cauchy-Schwarz step, which is an equality
+    when the sum has a single term: for one visibility |e(x, y)|^2 = w |V|^2 * w |b(x, y)|^2
+    at every pixel, and for a one-pixel model the prediction error of every visibility is
+    |I_p|^2 |b_k(x_p, y_p)|^2. A bound inflated by a slip (a doubled sum, a lost factor h,
+    a wrong sign in b) fails here, where an inequality test would still pass."""
+    n_img, N = 32, 64
+    T, x, hvec, uv = setup(n_img, N, W, Ms, interp, 6, seed=11)
+    for k in range(uv.shape[0]):
+        u, v = uv[k:k + 1, 0], uv[k:k + 1, 1]
+        plan = I.Plan(u, v, W, N)
+        V = np.array([0.7 - 1.3j])
+        w = np.array([1.7])
+        img = I.dirty_image(plan, T, Ms, interp, hvec, n_img, V, w)
+        ref = I.dft_dirty_image(u, v, V, w, x, x)
+        bound = I.image_bound(plan, T, Ms, interp, u, v, V, w, x, x, hvec)
+        err2 = np.abs(img - ref) ** 2
+        np.testing.assert_allclose(err2, bound, rtol=1e-6, atol=1e-26 * float(np.abs(V[0]) ** 2 * w[0] ** 2))
+    # prediction from a model with one non-zero pixel (p, q)
+    plan = I.Plan(uv[:, 0], uv[:, 1], W, N)
+    for p, q in [(5, 9), (16, 16), (0, 31)]:
+        model = np.zeros((n_img, n_img), dtype=np.complex128)
+        model[p, q] = 2.0 + 0.5j
+        pv = I.predict_vis(plan, T, Ms, interp, hvec, model)
+        ref = I.dft_predict(uv[:, 0], uv[:, 1], model, x, x)
+        bound = I.predict_bound(plan, T, Ms, interp, uv[:, 0], uv[:, 1], model[p:p + 1, q:q + 1],
+                                x[q:q + 1], x[p:p + 1], hvec[q:q + 1], hvec[p:p + 1])
+        np.testing.assert_allclose(np.abs(pv - ref) ** 2, bound, rtol=1e-6, atol=1e-28)
