@@ -41,6 +41,10 @@ WORKLOAD = dict(n_ant=64, hours=6.0, n_times=2048, freq_hz=1.4e9, n_src=200, noi
 WORKLOAD_NAME = ("64-antenna 6 h Earth-rotation tracks (2048 samples, 1.4 GHz, dec -30), 4,128,768 vis, "
                  "200 point sources + noise, 4096^2 grid, 2048^2 image, W=7, linear table M_s=1000, complex64")
 L2_FLUSH_BYTES = 256 << 20
+CLOCK_WINDOW_S = 2.2  # the clock record spans the timed steps plus identical steps up to this long
+VALUE_DEFINITION = ("value = visibilities / time of one whole step (bin + grid + FFT + crop/correct + pad/correct + "
+                    "FFT + degrid); grid_degrid_mvis_s = visibilities / (grid + degrid kernel time), the narrower "
+                    "figure of the metric's name")
 KERNELS_PER_STEP = 11  # bin 6, grid sweep + spill 2, crop 1, pad 1, degrid sweep 1
 
 
@@ -113,30 +117,102 @@ def oracle_setup():
     return _ORACLE_SETUP["T"], _ORACLE_SETUP["hv"]
 
 
-ORACLE_SAMPLE = 16  # the oracle processes every 16th visibility on the full 4096^2 grid
-
-
-def oracle_step_sample(uv, dl, vis, model):
-    """One oracle step (grid, FFT, crop, pad, FFT, degrid) on every ORACLE_SAMPLE-th
-    visibility, on the full grid; returns (visibilities processed, seconds)."""
+def oracle_step(uv, dl, vis, model, T, hv):
+    """One oracle step on the given visibilities with the full grid: grid, FFT (+i), correct
+    and crop; pad and correct the model, FFT (-i), degrid. Returns seconds per stage."""
     from oracle import imaging as I
     w = WORKLOAD
     N, n_img, W, Ms = w["N"], w["n_image"], w["W"], w["oversample"]
-    T, hv = oracle_setup()
-    sel = np.arange(0, uv.shape[0], ORACLE_SAMPLE)
     t0 = time.perf_counter()
-    uc = I.cells_from_wavelengths(uv[sel], N, dl)
+    uc = I.cells_from_wavelengths(uv, N, dl)
     plan = I.Plan(uc[:, 0], uc[:, 1], W, N)
-    img = I.dirty_image(plan, T, Ms, 1, hv, n_img, vis[sel].astype(np.complex128))
-    pv = I.predict_vis(plan, T, Ms, 1, hv, model.astype(np.complex128))
-    dt = time.perf_counter() - t0
+    G = I.grid(plan, T, Ms, 1, np.asarray(vis, dtype=np.complex128))
+    t1 = time.perf_counter()
+    img = I.correct_crop(I.fft_image(G), hv, n_img)
+    del G
+    Gm = I.model_grid(I.pad_correct(np.asarray(model, dtype=np.complex128), hv, N))
+    t2 = time.perf_counter()
+    pv = I.degrid(plan, T, Ms, 1, Gm)
+    t3 = time.perf_counter()
     assert np.isfinite(img).all() and np.isfinite(pv).all()
-    return sel.size, dt
+    return {"grid": t1 - t0, "fft_correct": t2 - t1, "degrid": t3 - t2, "total": t3 - t0}
 
 
-def oracle_sample_text(n, nv):
-    return (f"one oracle step on every {ORACLE_SAMPLE}th visibility ({n} of {nv}) with the full 4096^2 grid, "
-            f"FFTs and correction; value = visibilities of the sample per second; single-threaded numpy float64")
+def _oracle_worker(idx, uv, dl, vis, model, T, hv, n_steps, barrier, queue):
+    """One host core of the all-core oracle: n_steps steps on its share of the visibilities,
+    each started together with the other workers' at a barrier."""
+    for k in range(n_steps):
+        barrier.wait()
+        st = oracle_step(uv, dl, vis, model, T, hv)
+        queue.put((idx, k, int(uv.shape[0]), st))
+
+
+def oracle_workers():
+    """Worker count for the all-core oracle: every host core, as far as memory allows
+    (a worker holds about 2.5 GB at the 4096^2 grid)."""
+    cores = os.cpu_count() or 1
+    try:
+        mem = os.sysconf("SC_PHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+        cores = max(1, min(cores, int(mem // (2.5 * 2 ** 30))))
+    except (ValueError, OSError, AttributeError):
+        pass
+    return cores
+
+
+def oracle_allcore(uv, dl, vis, model, n_steps, every=1):
+    """The oracle on every host core: the visibilities sel = every `every`-th are dealt to P
+    spawned worker processes (one core each), each runs a whole oracle step on its share
+    (its own full-size grid and FFTs). Returns (P, visibilities per step, list of wall
+    seconds per step from the common start to the last worker's result, per-stage
+    seconds of the slowest worker of the last step)."""
+    import multiprocessing as mp
+    T, hv = oracle_setup()
+    P = oracle_workers()
+    sel = np.arange(0, uv.shape[0], every)
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(P + 1)
+    queue = ctx.Queue()
+    env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env:
+        os.environ[k] = "1"
+    procs = []
+    try:
+        for p in range(P):
+            part = sel[p::P]
+            procs.append(ctx.Process(target=_oracle_worker,
+                                     args=(p, np.ascontiguousarray(uv[part]), dl, np.ascontiguousarray(vis[part]),
+                                           model, T, hv, n_steps, barrier, queue), daemon=True))
+            procs[-1].start()
+    finally:
+        for k, v in env.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    walls, last = [], None
+    for k in range(n_steps):
+        barrier.wait()
+        t0 = time.perf_counter()
+        res = [queue.get() for _ in range(P)]
+        walls.append(time.perf_counter() - t0)
+        last = max((r[3] for r in res), key=lambda st: st["total"])
+    for pr in procs:
+        pr.join(timeout=60)
+    return P, int(sel.size), walls, last
+
+
+def oracle_single(uv, dl, vis, model, every):
+    """The oracle on one core (this process) on every `every`-th visibility."""
+    T, hv = oracle_setup()
+    sel = np.arange(0, uv.shape[0], every)
+    st = oracle_step(uv[sel], dl, vis[sel], model, T, hv)
+    return int(sel.size), st
+
+
+ALLCORE_TEXT = ("the FP64 oracle (numpy) on {P} host cores: the {n} visibilities ({frac}) dealt to {P} spawned "
+                "processes, each running a whole oracle step (grid, FFT, crop, pad, FFT, degrid) on its share with "
+                "its own 4096^2 grid; value = visibilities per second from the common start to the last result "
+                "(the {P} partial dirty images are not summed)")
 
 
 def run_reference(args):
@@ -145,20 +221,18 @@ def run_reference(args):
         return
     uv, dl, vis, model = make_inputs()
     nv = uv.shape[0]
-    times = []
-    for _ in range(args.warmup):
-        oracle_step_sample(uv, dl, vis, model)
-    for _ in range(args.steps):
-        n, dt = oracle_step_sample(uv, dl, vis, model)
-        times.append(dt)
-    step_s = float(np.mean(times))
+    P, n, walls, last = oracle_allcore(uv, dl, vis, model, args.warmup + args.steps)
+    timed = walls[args.warmup:]
+    step_s = float(np.mean(timed))
     value = n / step_s / 1e6
+    sample = ALLCORE_TEXT.format(P=P, n=n, frac="all of them")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mvis/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_s,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD_NAME, "parallelism": "none (host oracle)"},
-            "cpu_baseline": {"value": value, "unit": "Mvis/s", "cores": 1, "kind": "oracle",
-                             "sample": oracle_sample_text(n, nv)},
+            "data": "synthetic", "config": {"workload": WORKLOAD_NAME, "parallelism": f"{P} host processes"},
+            "value_definition": VALUE_DEFINITION,
+            "oracle_stage_s_slowest_worker": last,
+            "cpu_baseline": {"value": value, "unit": "Mvis/s", "cores": P, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "Mvis/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -173,9 +247,11 @@ class Clocks:
     sampling interval)."""
 
     def __init__(self, index):
+        import tempfile
         self.proc = None
         self.index = index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        fd, self.path = tempfile.mkstemp(prefix=f"lmg_clocks_rank{index}_", suffix=".csv")
+        os.close(fd)
         self.first = 0
 
     def _lines(self):
@@ -219,9 +295,14 @@ class Clocks:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.f.close()
+        lines = self._lines()[self.first:]
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self._lines()[self.first:]:
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             try:
                 sm.append(float(parts[1]))
@@ -356,9 +437,28 @@ def run_native(args):
     t_wall = time.perf_counter() - t_wall
     if world > 1:
         torch.distributed.barrier()
-    clk = clocks.stop()
     step_ms = max_over_ranks(float(np.mean([s.elapsed_time(e) for s, e in zip(starts, ends)])), dev)
     value = whole_job_mvis(nv, world, step_ms)
+    # The K timed steps of this workload last about K ms, too short for a clock record of
+    # nvidia-smi samples, so identical steps (L2 flushed the same way) continue right after
+    # them until the window is CLOCK_WINDOW_S long; the clocks are taken over the whole
+    # window and the soak's own time per step is reported beside the timed one.
+    soak_n, soak_ms = 0, []
+    t_soak = time.perf_counter()
+    while time.perf_counter() - t_soak + t_wall < CLOCK_WINDOW_S:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(50):
+            flush.zero_()
+            a.record(stream)
+            step()
+            b.record(stream)
+        torch.cuda.synchronize()
+        soak_ms.append(a.elapsed_time(b))
+        soak_n += 50
+    clk = clocks.stop()
+    clk["window"] = (f"{args.steps} timed steps followed by {soak_n} identical steps "
+                     f"({t_wall + time.perf_counter() - t_soak:.2f} s of steps)")
+    clk["soak_ms_per_step"] = float(np.mean(soak_ms)) if soak_ms else None
 
     # per-stage breakdown (untimed by the driver's clock; same stream, events per stage)
     stages = {}
@@ -455,18 +555,36 @@ def run_native(args):
     h2d = uv_h.numel() * 8 + vis_h.numel() * 8 + model_h.numel() * 8
     d2h = img_h.numel() * 8 + pv_h.numel() * 8
 
-    # roofline of the gridding pass (sweep + spill): algorithmic bytes per launch
-    grid_bytes = nv * (16 + 8) + w["N"] * w["N"] * 8
+    # roofline of the dominant sweep pass (gridding = sweep + spill, degridding = zeroing +
+    # sweep; whichever took longer): algorithmic bytes per launch and the arithmetic side
+    # 4 W^2 flops per visibility per pass, against the measured HBM copy bandwidth and the
+    # float32 FMA rate measured here on this device
+    pass_bytes = nv * (16 + 8) + w["N"] * w["N"] * 8
+    pass_flops = 4 * w["W"] ** 2 * nv
     peak, peak_src = measured_peak_hbm()
-    achieved = grid_bytes / (stages["grid"] * 1e-3) / 1e9
-    roof = {"kernel": "k_grid_sweep + k_grid_spill (gridding pass)", "bound": "hbm", "achieved": achieved,
-            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic_record(),
-            "algorithmic_bytes": grid_bytes, "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs, burst)"}
-    degrid_bytes = grid_bytes
-    extra = {"stages_ms": stages,
+    fp32 = lmg.fp32_fma_rate() / 1e12
+    dom = "grid" if stages["grid"] >= stages["degrid"] else "degrid"
+    t_dom = stages[dom] * 1e-3
+    achieved = pass_bytes / t_dom / 1e9
+    t_hbm = pass_bytes / (peak * 1e9)
+    t_alu = pass_flops / (fp32 * 1e12)
+    roof = {"kernel": ("k_grid_sweep + k_grid_spill (gridding pass)" if dom == "grid"
+                       else "k_degrid_sweep with its output zeroing (degridding pass)"),
+            "bound": "hbm" if t_hbm >= t_alu else "alu", "achieved": achieved,
+            "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic_record() if dom == "grid" else None,
+            "algorithmic_bytes": pass_bytes, "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs, burst)",
+            "fp32_side": {"flops": pass_flops, "peak_tflops": fp32, "achieved_tflops": pass_flops / t_dom / 1e12,
+                          "frac": pass_flops / t_dom / 1e12 / fp32,
+                          "peak_source": "measured in this process: lmg_fp32_fma_rate (fmaf chains on every SM)",
+                          "derivation": "4 W^2 flops per visibility per pass (8 W^2 for gridding plus degridding); "
+                                        f"time at peak {1e6 * t_alu:.1f} us against {1e6 * t_hbm:.1f} us for the "
+                                        "algorithmic bytes at the HBM peak"}}
+    other = "degrid" if dom == "grid" else "grid"
+    extra = {"stages_ms": stages, "value_definition": VALUE_DEFINITION,
              "grid_degrid_mvis_s": nv / ((stages["grid"] + stages["degrid"]) * 1e-3) / 1e6,
              "bin_grid_degrid_mvis_s": nv / ((stages["bin"] + stages["grid"] + stages["degrid"]) * 1e-3) / 1e6,
-             "degrid_roofline_frac": degrid_bytes / (stages["degrid"] * 1e-3) / 1e9 / peak,
+             f"{other}_roofline_frac": pass_bytes / (stages[other] * 1e-3) / 1e9 / peak,
              "timed_wall_s": t_wall}
 
     line = {"metric": METRIC, "value": value, "unit": "Mvis/s", "n_gpus": world, "steps": args.steps,
@@ -487,9 +605,16 @@ def run_native(args):
         torch.cuda.synchronize()
         line["accuracy_vs_fp64"] = accuracy(uv, dl, vis, model, img_d.cpu().numpy(), pv_d.cpu().numpy())
     if rank == 0 and not args.no_cpu_baseline:
-        n, dt = oracle_step_sample(uv, dl, vis, model)
-        line["cpu_baseline"] = {"value": n / dt / 1e6, "unit": "Mvis/s", "cores": 1, "kind": "oracle",
-                                "sample": oracle_sample_text(n, nv) + f"; {dt:.1f} s"}
+        P, n, walls, last = oracle_allcore(uv, dl, vis, model, 1, every=2)
+        n1, st1 = oracle_single(uv, dl, vis, model, every=8)
+        line["cpu_baseline"] = {
+            "value": n / walls[0] / 1e6, "unit": "Mvis/s", "cores": P, "kind": "oracle",
+            "sample": ALLCORE_TEXT.format(P=P, n=n, frac="every 2nd") + f"; {walls[0]:.1f} s",
+            "os_cpu_count": os.cpu_count(), "stage_s_slowest_worker": last,
+            "single_core": {"value": n1 / st1["total"] / 1e6, "unit": "Mvis/s", "cores": 1,
+                            "grid_degrid_mvis_s": n1 / (st1["grid"] + st1["degrid"]) / 1e6, "stage_s": st1,
+                            "sample": f"one oracle step in this process on every 8th visibility ({n1}) with the "
+                                      f"full 4096^2 grid; {st1['total']:.1f} s"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

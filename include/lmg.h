@@ -57,7 +57,8 @@ typedef enum {
   LMG_ECUDA = -3,         /* a CUDA runtime call or kernel launch failed */
   LMG_ECUFFT = -4,        /* a cuFFT call failed */
   LMG_EUNSUPPORTED = -5,  /* valid request this build does not implement */
-  LMG_ENOCONV = -6        /* the least-misfit optimisation did not converge */
+  LMG_ENOCONV = -6,       /* the least-misfit optimisation did not converge */
+  LMG_EDEVICE = -7        /* a kernel's own check found an anomaly (lmg_plan_status) */
 } lmg_status;
 
 enum { LMG_C64 = 0, LMG_C128 = 1 };
@@ -143,6 +144,15 @@ int lmg_correction_export(const lmg_table* t, int64_t n_image, int single_precis
  * Returns LMG_EINVAL, LMG_ENOMEM, LMG_ECUDA or LMG_ECUFFT on failure. */
 int lmg_plan_create(const lmg_table* t, int64_t n_image, double pixel_scale,
                     int64_t max_vis, int dtype, lmg_plan** out);
+
+/* lmg_plan_create_ex -- lmg_plan_create with flags. LMG_PLAN_NO_WORK_GRIDS leaves out the
+ * plan's two [N][N] grids (work and model, 2 N^2 complex: 268 MB for a complex64 4096^2
+ * grid); such a plan images and predicts only through lmg_dirty_image_ws and
+ * lmg_predict_vis_ws with caller workspace (lmg_dirty_image / lmg_predict_vis return
+ * LMG_EINVAL on it, lmg_work_grid returns NULL). Unknown flags are LMG_EINVAL. */
+#define LMG_PLAN_NO_WORK_GRIDS 1
+int lmg_plan_create_ex(const lmg_table* t, int64_t n_image, double pixel_scale,
+                       int64_t max_vis, int dtype, int flags, lmg_plan** out);
 int lmg_plan_free(lmg_plan* p);
 
 /* lmg_plan_bin -- bin visibility positions for gridding and degridding (support rule of
@@ -187,7 +197,9 @@ int lmg_fft(lmg_plan* p, int direction, void* grid, void* stream);
  * lmg_grid_correct with LMG_PAD). */
 int lmg_fft_pruned(lmg_plan* p, int direction, void* grid, void* stream);
 
-/* lmg_grid_correct -- grid correction and crop (Eqs. 4, 15), or its adjoint.
+/* lmg_grid_correct -- grid correction and crop (Eqs. 4, 15), or its adjoint, with the
+ * plan's device copy of the correction factors (the table object is host-only and holds no
+ * device memory; lmg_correct_factors takes the factors from the caller instead).
  *   LMG_CROP: in = FFT output [N][N] of a grid in index order, out = image
  *             [n_image][n_image] with out[p][q] = h(y_p) h(x_q) F(x_q, y_p).
  *   LMG_PAD:  in = image [n_image][n_image], out = [N][N] array that LMG_FFT_MODEL turns
@@ -196,13 +208,58 @@ int lmg_fft_pruned(lmg_plan* p, int direction, void* grid, void* stream);
 int lmg_grid_correct(lmg_plan* p, int direction, const void* in, void* out, void* stream);
 
 /* lmg_dirty_image -- grid, FFT (+i), correct and crop into image_out [n_image][n_image],
- * using the plan's work grid. Allocates nothing. */
+ * using the plan's work grid (lmg_dirty_image_ws takes a caller workspace). Allocates
+ * nothing. */
 int lmg_dirty_image(lmg_plan* p, const void* vis, const void* weights, int accum,
                     void* image_out, void* stream);
 
 /* lmg_predict_vis -- pad and correct image [n_image][n_image], FFT (-i), degrid into
  * vis_out [nvis], using the plan's work grid. Allocates nothing. */
 int lmg_predict_vis(lmg_plan* p, const void* image, void* vis_out, void* stream);
+
+/* lmg_workspace_bytes -- bytes of caller workspace that lmg_dirty_image_ws and
+ * lmg_predict_vis_ws need for this plan: one [N][N] complex grid of the plan's dtype
+ * (N^2 * 8 bytes for LMG_C64, N^2 * 16 for LMG_C128). 0 for a NULL plan. */
+size_t lmg_workspace_bytes(const lmg_plan* p);
+
+/* lmg_dirty_image_ws -- lmg_dirty_image with a caller-owned device workspace in place of
+ * the plan's work grid (Eqs. 4-6: grid, FFT (+i) pruned to the kept columns, correct and
+ * crop). workspace: device, 256-byte aligned, ws_bytes >= lmg_workspace_bytes(p); its
+ * contents on entry do not matter and on return are the partially transformed grid.
+ * Allocates nothing. LMG_EINVAL for a NULL, misaligned or short workspace. */
+int lmg_dirty_image_ws(lmg_plan* p, const void* vis, const void* weights, int accum,
+                       void* image_out, void* workspace, size_t ws_bytes, void* stream);
+
+/* lmg_predict_vis_ws -- lmg_predict_vis with a caller-owned device workspace (Section 4:
+ * pad and correct into the whole workspace, zero outside the kept field; FFT (-i) of the
+ * kept rows then every column, in place; degrid). Same workspace rules as
+ * lmg_dirty_image_ws. Allocates nothing. */
+int lmg_predict_vis_ws(lmg_plan* p, const void* image, void* vis_out, void* workspace,
+                       size_t ws_bytes, void* stream);
+
+/* lmg_correct_factors -- the grid correction of lmg_grid_correct with caller-supplied
+ * factors instead of a plan (Eqs. 4, 15): h is a device array of n_image reals (float for
+ * LMG_C64, double for LMG_C128), h[p] = h(x_p) at x_p = (p - n_image/2) / N, for example
+ * lmg_correction_export's values copied to the device. LMG_CROP: in [N][N] FFT output,
+ * out [n_image][n_image]; LMG_PAD: in [n_image][n_image], out [N][N] (zero outside the
+ * kept pixels). n_image even, N even in [n_image, 65536]. Allocates nothing. */
+int lmg_correct_factors(int direction, const void* in, void* out, const void* h, int64_t n_image,
+                        int64_t N, int dtype, void* stream);
+
+/* lmg_plan_status -- device status of the plan's last binning. The kernels check their own
+ * bounds and record what they could not do in a status word instead of faulting (today:
+ * more work items than the plan's capacity, whose excess is dropped; the capacity is sized
+ * so that this does not happen for any input within max_vis). Synchronises the stream,
+ * writes the status bits to *status_bits (may be NULL) and returns LMG_OK when they are
+ * zero, LMG_EDEVICE with a message otherwise. */
+int lmg_plan_status(lmg_plan* p, int* status_bits, void* stream);
+
+/* lmg_fp32_fma_rate -- measured float32 FMA throughput of the current device in flop/s (a
+ * kernel of independent fmaf chains filling every SM, best of three timed launches after
+ * one warm-up; synchronises the stream). A measurement helper for the arithmetic side of the
+ * sweeps' roofline (8 W^2 flops per visibility for gridding plus degridding); not part of the
+ * paper's method. */
+int lmg_fp32_fma_rate(double* flops_per_s, void* stream);
 
 /* lmg_plan_info -- sizes of a plan: out[0] = N, out[1] = n_image, out[2] = W,
  * out[3] = nvis of the last binning, out[4] = records, out[5] = work items (records and
@@ -234,10 +291,16 @@ void* lmg_work_grid(lmg_plan* p);
  *   vis          device complex64 [nvis]; weights device float32 [nvis] or NULL
  *   grid         device complex64 [N][N]; every cell is overwritten
  * The first call on a device (with that device current) looks up the array's device
- * address and records it; make that first call before any stream capture. All calls
- * share the one array: calls whose GPU work overlaps (other streams, other host threads)
- * race on it and must be serialised by the caller. Nothing is carried between calls
- * (bucket counts and counters are cleared on the stream by each call). */
+ * address and records it; make that first call before any stream capture. The recorded
+ * address belongs to the device's current context: do not call lmg_grid_static again after
+ * cudaDeviceReset on that device (the array then lives at a new address that this library
+ * does not look up again). Each device keeps the float32 copy of the table of its latest
+ * call; a call with a table whose values differ uploads it from host memory (and returns
+ * LMG_EUNSUPPORTED if its stream is being captured), a call with the same table skips
+ * the upload. All calls share the one array: calls whose GPU work overlaps (other streams,
+ * other host threads) race on it and must be serialised by the caller. Nothing else is
+ * carried between calls (bucket counts and counters are cleared on the stream by each
+ * call). */
 #define LMG_STATIC_MAX_VIS 262144
 #define LMG_STATIC_MAX_N 2048
 #define LMG_STATIC_MAX_OVERSAMPLE 4096

@@ -4,6 +4,7 @@
 #include <cufft.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -16,6 +17,21 @@
 namespace lmg {
 namespace {
 thread_local std::string g_error;
+}
+// Host-side fault injection for tests of the error paths. The environment variable
+// LMG_INJECT_FAULT names one failure point; the library then reports that failure in place
+// of the call it stands for, without making that call:
+//   host_alloc    host allocation of a table object           -> LMG_ENOMEM
+//   device_alloc  every device allocation of a plan            -> LMG_ENOMEM
+//   cufft_plan    cuFFT plan creation of a plan                -> LMG_ECUFFT
+//   item_cap      plans get a work-item capacity of one item, so that the binning of any
+//                 input with more than one item exceeds it: the binning's own bounds
+//                 check drops the excess and records it in the device status word
+//                 (lmg_plan_status -> LMG_EDEVICE)
+// Nothing is injected on the GPU itself: no kernel is made to fault or wait.
+bool inject_fault(const char* point) {
+  const char* v = std::getenv("LMG_INJECT_FAULT");
+  return v != nullptr && std::strcmp(v, point) == 0;
 }
 int set_error(int status, const std::string& msg) {
   g_error = msg;
@@ -51,6 +67,8 @@ bool check_table_args(int W, double x0, int Ms, int interp, int correction) {
 template <typename T> int dalloc(T** p, size_t count, const char* what) {
   *p = nullptr;
   if (count == 0) count = 1;
+  if (inject_fault("device_alloc"))
+    return set_error(LMG_ENOMEM, std::string("device allocation of ") + what + " failed: injected (LMG_INJECT_FAULT)");
   cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * count);
   if (e != cudaSuccess) {
     *p = nullptr;
@@ -245,20 +263,12 @@ int plan_create(const lmg_table* t, int64_t n_image, double pixel_scale, int64_t
   p->Wp = dtype == LMG_C128 ? ((p->W + 1) & ~1) : (p->W | 1);
   const int nblk = int((N + opt.min_rows_per_block - 1) / opt.min_rows_per_block);
   p->item_cap = p->n_strips * nblk + int((2 * max_vis) / opt.min_item_target) + 2;
+  if (inject_fault("item_cap")) p->item_cap = 1;
   const long long L = (long long)p->n_strips * N;
   p->nchunks = bin_scan_chunks(L);
 
   int rc;
-  cudaError_t e = cudaGetDevice(&p->device);
-  if (e != cudaSuccess) {
-    delete p;
-    return cuda_error(e, "cudaGetDevice");
-  }
-  e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
-  if (e != cudaSuccess) {
-    delete p;
-    return cuda_error(e, "cudaDeviceGetAttribute");
-  }
+  cudaError_t e;
   // Device table (rows padded to Wp) and correction factors in the plan's precision.
   std::vector<double> hcorr(static_cast<size_t>(n_image));
   correction_factors(t, n_image, N, dtype == LMG_C64, hcorr.data());
@@ -303,6 +313,13 @@ int plan_create(const lmg_table* t, int64_t n_image, double pixel_scale, int64_t
     free_plan(p);
     return rc;
   }
+  // the device is queried after the allocations (which run on the current device), so
+  // that an injected allocation failure is reported before any CUDA call
+  if ((e = cudaGetDevice(&p->device)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device)) != cudaSuccess) {
+    free_plan(p);
+    return cuda_error(e, "device query");
+  }
   if ((e = cudaMemcpy(p->d_table, tab_bytes.data(), tab_bytes.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(p->d_h, h_bytes.data(), h_bytes.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemset(p->counters, 0, kNumCounters * sizeof(int))) != cudaSuccess ||
@@ -336,6 +353,10 @@ int plan_create(const lmg_table* t, int64_t n_image, double pixel_scale, int64_t
   }
   p->blocks_degrid = p->sms * (bps > 0 ? bps : 1);
   if (opt.fft) {
+    if (inject_fault("cufft_plan")) {
+      free_plan(p);
+      return set_error(LMG_ECUFFT, "cufftPlan2d failed: injected (LMG_INJECT_FAULT)");
+    }
     const cufftResult fr = cufftPlan2d(&p->fft, int(N), int(N), dtype == LMG_C128 ? CUFFT_Z2Z : CUFFT_C2C);
     if (fr != CUFFT_SUCCESS) {
       free_plan(p);
@@ -400,8 +421,8 @@ int lmg_kernel_table(int W, double x0, int oversample, int interp, int correctio
   if (!out) return set_error(LMG_EINVAL, "out is NULL");
   *out = nullptr;
   if (!check_table_args(W, x0, oversample, interp, correction)) return LMG_EINVAL;
-  lmg_table* t = new (std::nothrow) lmg_table;
-  if (!t) return set_error(LMG_ENOMEM, "host allocation failed");
+  lmg_table* t = inject_fault("host_alloc") ? nullptr : new (std::nothrow) lmg_table;
+  if (!t) return set_error(LMG_ENOMEM, "host allocation of the table failed");
   t->W = W;
   t->x0 = x0;
   t->x0p = 0.5 * x0;
@@ -431,8 +452,8 @@ int lmg_table_from_values(int W, double x0, int oversample, int interp, int corr
   if (!check_table_args(W, x0, oversample, interp, correction)) return LMG_EINVAL;
   if (interp == LMG_INTERP_DIRECT)
     return set_error(LMG_EINVAL, "LMG_INTERP_DIRECT needs a least-misfit table from lmg_kernel_table");
-  lmg_table* t = new (std::nothrow) lmg_table;
-  if (!t) return set_error(LMG_ENOMEM, "host allocation failed");
+  lmg_table* t = inject_fault("host_alloc") ? nullptr : new (std::nothrow) lmg_table;
+  if (!t) return set_error(LMG_ENOMEM, "host allocation of the table failed");
   t->W = W;
   t->x0 = x0;
   t->x0p = 0.5 * x0;
@@ -600,6 +621,7 @@ int lmg_dirty_image(lmg_plan* p, const void* vis, const void* weights, int accum
   clear_error();
   if (!p || !image_out) return set_error(LMG_EINVAL, "NULL argument");
   if (int rc = need_binned(p)) return rc;
+  if (!p->work) return set_error(LMG_EINVAL, "plan has no work grid (LMG_PLAN_NO_WORK_GRIDS): use lmg_dirty_image_ws");
   if (p->nvis > 0 && !vis) return set_error(LMG_EINVAL, "vis is NULL");
   if (accum != LMG_ACCUM_PLAIN && accum != LMG_ACCUM_COMPENSATED) return set_error(LMG_EINVAL, "bad accum");
   if (accum == LMG_ACCUM_COMPENSATED && p->dtype != LMG_C64)
@@ -617,12 +639,103 @@ int lmg_predict_vis(lmg_plan* p, const void* image, void* vis_out, void* stream)
   clear_error();
   if (!p || !image) return set_error(LMG_EINVAL, "NULL argument");
   if (int rc = need_binned(p)) return rc;
+  if (!p->work) return set_error(LMG_EINVAL, "plan has no work grids (LMG_PLAN_NO_WORK_GRIDS): use lmg_predict_vis_ws");
   if (p->nvis > 0 && !vis_out) return set_error(LMG_EINVAL, "vis_out is NULL");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int rc = launch_status(pad_rows_launch(image, p->model, p->d_h, int(p->n_image), int(p->N), p->dtype, st), "pad");
   if (rc == LMG_OK) rc = fft_model_to_work(p, st);
   if (rc == LMG_OK) rc = do_degrid(p, p->work, vis_out, st);
   return rc;
+}
+
+int lmg_plan_create_ex(const lmg_table* t, int64_t n_image, double pixel_scale, int64_t max_vis, int dtype, int flags,
+                       lmg_plan** out) {
+  clear_error();
+  if (flags & ~LMG_PLAN_NO_WORK_GRIDS) return set_error(LMG_EINVAL, "unknown plan flags");
+  PlanOptions opt{};
+  opt.work_grid = (flags & LMG_PLAN_NO_WORK_GRIDS) == 0;
+  return plan_create(t, n_image, pixel_scale, max_vis, dtype, opt, out);
+}
+
+size_t lmg_workspace_bytes(const lmg_plan* p) {
+  if (!p) return 0;
+  return size_t(p->N) * size_t(p->N) * (p->dtype == LMG_C128 ? 16 : 8);
+}
+
+namespace {
+int check_workspace(const lmg_plan* p, const void* ws, size_t ws_bytes) {
+  if (!ws) return set_error(LMG_EINVAL, "workspace is NULL");
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return set_error(LMG_EINVAL, "workspace must be 256-byte aligned");
+  if (ws_bytes < lmg_workspace_bytes(p))
+    return set_error(LMG_EINVAL, "workspace too small: lmg_workspace_bytes gives " +
+                                     std::to_string(lmg_workspace_bytes(p)) + " bytes");
+  if (!p->fft_pruned_ok) return set_error(LMG_EUNSUPPORTED, "plan has no FFT plans");
+  return LMG_OK;
+}
+}  // namespace
+
+int lmg_dirty_image_ws(lmg_plan* p, const void* vis, const void* weights, int accum, void* image_out, void* workspace,
+                       size_t ws_bytes, void* stream) {
+  clear_error();
+  if (!p || !image_out) return set_error(LMG_EINVAL, "NULL argument");
+  if (int rc = need_binned(p)) return rc;
+  if (int rc = check_workspace(p, workspace, ws_bytes)) return rc;
+  if (p->nvis > 0 && !vis) return set_error(LMG_EINVAL, "vis is NULL");
+  if (accum != LMG_ACCUM_PLAIN && accum != LMG_ACCUM_COMPENSATED) return set_error(LMG_EINVAL, "bad accum");
+  if (accum == LMG_ACCUM_COMPENSATED && p->dtype != LMG_C64)
+    return set_error(LMG_EUNSUPPORTED, "compensated accumulation is for LMG_C64");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = do_grid(p, vis, weights, accum, workspace, st);
+  if (rc == LMG_OK) rc = fft_image_pruned(p, workspace, st);
+  if (rc == LMG_OK)
+    rc = launch_status(crop_correct_launch(workspace, image_out, p->d_h, int(p->n_image), int(p->N), p->dtype, st),
+                       "crop");
+  return rc;
+}
+
+int lmg_predict_vis_ws(lmg_plan* p, const void* image, void* vis_out, void* workspace, size_t ws_bytes, void* stream) {
+  clear_error();
+  if (!p || !image) return set_error(LMG_EINVAL, "NULL argument");
+  if (int rc = need_binned(p)) return rc;
+  if (int rc = check_workspace(p, workspace, ws_bytes)) return rc;
+  if (p->nvis > 0 && !vis_out) return set_error(LMG_EINVAL, "vis_out is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the whole workspace is written (zero outside the kept pixels), then transformed in place
+  int rc = launch_status(pad_correct_launch(image, workspace, p->d_h, int(p->n_image), int(p->N), p->dtype, st), "pad");
+  if (rc == LMG_OK) rc = fft_model_pruned(p, workspace, st);
+  if (rc == LMG_OK) rc = do_degrid(p, workspace, vis_out, st);
+  return rc;
+}
+
+int lmg_correct_factors(int direction, const void* in, void* out, const void* h, int64_t n_image, int64_t N, int dtype,
+                        void* stream) {
+  clear_error();
+  if (!in || !out || !h) return set_error(LMG_EINVAL, "NULL argument");
+  if (n_image < 2 || (n_image & 1) || N < n_image || (N & 1) || N > 65536)
+    return set_error(LMG_EINVAL, "need even n_image >= 2 and even N in [n_image, 65536]");
+  if (dtype != LMG_C64 && dtype != LMG_C128) return set_error(LMG_EINVAL, "dtype must be LMG_C64 or LMG_C128");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc;
+  if (direction == LMG_CROP) rc = crop_correct_launch(in, out, h, int(n_image), int(N), dtype, st);
+  else if (direction == LMG_PAD) rc = pad_correct_launch(in, out, h, int(n_image), int(N), dtype, st);
+  else return set_error(LMG_EINVAL, "direction must be LMG_CROP or LMG_PAD");
+  return launch_status(rc, "grid correction");
+}
+
+int lmg_plan_status(lmg_plan* p, int* status_bits, void* stream) {
+  clear_error();
+  if (!p) return set_error(LMG_EINVAL, "plan is NULL");
+  int c[kNumCounters];
+  cudaError_t e = cudaMemcpyAsync(c, p->counters, sizeof(c), cudaMemcpyDeviceToHost, static_cast<cudaStream_t>(stream));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_error(e, "reading the device status");
+  int bits = c[kCntStatus];
+  if (static_cast<long long>(c[kCntItems]) + c[kCntItemsBack] > p->item_cap) bits |= kStatusItemOverflow;
+  if (status_bits) *status_bits = bits;
+  if (bits & kStatusItemOverflow)
+    return set_error(LMG_EDEVICE, "binning produced more work items than the plan holds; the excess was dropped");
+  if (bits) return set_error(LMG_EDEVICE, "device status " + std::to_string(bits));
+  return LMG_OK;
 }
 
 }  // extern "C"

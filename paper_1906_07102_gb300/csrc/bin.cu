@@ -283,6 +283,7 @@ __global__ void k_make_items(const int* __restrict__ offsets, int N, int n_strip
     if (2 * n > target) slot = atomicAdd(counters + kCntItems, 1);
     else slot = cap - 1 - atomicAdd(counters + kCntItemsBack, 1);
     if (slot >= 0 && slot < cap) items[slot] = Item{s, rb + r0, rb + r1, n};
+    else atomicOr(counters + kCntStatus, kStatusItemOverflow);
   }
 }
 

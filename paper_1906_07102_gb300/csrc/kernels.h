@@ -16,11 +16,16 @@ struct Item;
 enum {
   kCntBad = 0,         // dropped positions
   kCntItems = 1,       // items placed from the front (heavy)
-  // slot 2 is free
+  kCntStatus = 2,      // device status word: kStatus* bits set by the kernels' own checks
   kCntItemsBack = 3,   // items placed from the back (light)
   kCntGridWork = 4,    // work counter of the gridding sweep
   kCntDegridWork = 5,  // work counter of the degridding sweep
   kNumCounters = 8
+};
+
+// Device status bits (counters[kCntStatus]); the host reports them as LMG_EDEVICE.
+enum {
+  kStatusItemOverflow = 1,  // more work items than the plan's capacity: the excess was dropped
 };
 
 struct BinArgs {

@@ -16,6 +16,8 @@ namespace lmg {
 // Thread-local error message; set_error returns the status for `return set_error(...)`.
 int set_error(int status, const std::string& msg);
 void clear_error();
+// Host-side fault injection (LMG_INJECT_FAULT; see api.cu): true when `point` is named.
+bool inject_fault(const char* point);
 
 // Table design parameters (Appendix A node counts).
 constexpr int kNg = 32;

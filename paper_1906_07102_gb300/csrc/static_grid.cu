@@ -10,6 +10,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 #include <mutex>
 #include <string>
 
@@ -54,14 +55,37 @@ struct DeviceSetup {
   bool done = false;
   unsigned char* base = nullptr;  // device address of g_static_scratch
   int sms = 0;
+  bool staged = false;            // a table is in the scratch ...
+  unsigned long long staged_key = 0;  // ... with this content key (table_key)
 };
 constexpr int kMaxDevices = 64;
 DeviceSetup g_setup[kMaxDevices];
 std::mutex g_setup_mutex;
 
-// Host staging of the float32 table rows (copied to the scratch before each call).
+// Host staging of the float32 table rows (copied to the scratch when a call brings a table
+// that is not the one already staged on its device).
 float g_table_host[(kMaxOversample + 1) * kMaxWp];
 std::mutex g_table_mutex;
+
+// Content key of a table (FNV-1a over W, oversample, interpolation and the float32 values
+// the kernels read): equal keys mean the staged rows can be used as they are.
+unsigned long long table_key(const lmg_table* t) {
+  unsigned long long h = 1469598103934665603ull;
+  auto mix = [&h](unsigned v) {
+    h ^= v;
+    h *= 1099511628211ull;
+  };
+  mix(unsigned(t->W));
+  mix(unsigned(t->Ms));
+  mix(unsigned(t->interp));
+  for (double c : t->C) {
+    const float f = float(c);
+    unsigned u;
+    std::memcpy(&u, &f, sizeof(u));
+    mix(u);
+  }
+  return h;
+}
 
 int setup_device(int dev, DeviceSetup** out) {
   std::lock_guard<std::mutex> lock(g_setup_mutex);
@@ -117,14 +141,31 @@ extern "C" int lmg_grid_static(const lmg_table* t, int64_t n_image, double pixel
   unsigned char* base = s->base;
   const int W = t->W, Ms = t->Ms, Wp = W | 1;
 
-  // Table rows in float32, padded to Wp, into the scratch.
+  // Table rows in float32, padded to Wp, into the scratch -- only when this device does not
+  // already hold this table. The upload copies from pageable host memory, which a stream
+  // that is being captured cannot record, so it is refused there.
   {
     std::lock_guard<std::mutex> lock(g_table_mutex);
-    for (int i = 0; i <= Ms; ++i)
-      for (int j = 0; j < Wp; ++j)
-        g_table_host[size_t(i) * Wp + j] = j < W ? float(t->C[size_t(i) * W + j]) : 0.0f;
-    e = cudaMemcpyAsync(base + kOffTable, g_table_host, sizeof(float) * size_t(Ms + 1) * Wp, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return set_error(LMG_ECUDA, std::string("table upload: ") + cudaGetErrorString(e));
+    const unsigned long long key = table_key(t);
+    if (!s->staged || s->staged_key != key) {
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      e = cudaStreamIsCapturing(st, &cs);
+      if (e != cudaSuccess) return set_error(LMG_ECUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
+      if (cs != cudaStreamCaptureStatusNone)
+        return set_error(LMG_EUNSUPPORTED, "lmg_grid_static would upload a table not yet staged on this device, "
+                                           "and the stream is capturing; call it once with this table first");
+      for (int i = 0; i <= Ms; ++i)
+        for (int j = 0; j < Wp; ++j)
+          g_table_host[size_t(i) * Wp + j] = j < W ? float(t->C[size_t(i) * W + j]) : 0.0f;
+      e = cudaMemcpyAsync(base + kOffTable, g_table_host, sizeof(float) * size_t(Ms + 1) * Wp, cudaMemcpyHostToDevice,
+                          st);
+      if (e != cudaSuccess) {
+        s->staged = false;
+        return set_error(LMG_ECUDA, std::string("table upload: ") + cudaGetErrorString(e));
+      }
+      s->staged = true;
+      s->staged_key = key;
+    }
   }
 
   const int n_strips = int(N / kStrip);

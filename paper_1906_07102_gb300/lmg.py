@@ -18,6 +18,7 @@ CORRECTION = {"hopt": 0, "inv_c": 1}
 ACCUM = {"plain": 0, "compensated": 1}
 LMG_CROP, LMG_PAD = 0, 1
 FFT_IMAGE, FFT_MODEL = 1, -1
+PLAN_NO_WORK_GRIDS = 1
 
 _lib = None
 _vp = ctypes.c_void_p
@@ -53,6 +54,14 @@ _SIGS = {
     "lmg_batch_predict_vis": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "lmg_batch_tune": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "lmg_batch_info": (ctypes.c_int, [_vp, _vp]),
+    "lmg_plan_create_ex": (ctypes.c_int, [_vp, _i64, ctypes.c_double, _i64, ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(_vp)]),
+    "lmg_workspace_bytes": (ctypes.c_size_t, [_vp]),
+    "lmg_dirty_image_ws": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_size_t, _vp]),
+    "lmg_predict_vis_ws": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]),
+    "lmg_correct_factors": (ctypes.c_int, [ctypes.c_int, _vp, _vp, _vp, _i64, _i64, ctypes.c_int, _vp]),
+    "lmg_plan_status": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), _vp]),
+    "lmg_fp32_fma_rate": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), _vp]),
     "lmg_last_error": (ctypes.c_char_p, []),
     "lmg_version": (ctypes.c_char_p, []),
 }
@@ -145,13 +154,17 @@ class Table:
 class Plan:
     """Device state for one (table, image size, pixel scale); see lmg_plan_create."""
 
-    def __init__(self, table, n_image, pixel_scale, max_vis, dtype="c64"):
+    def __init__(self, table, n_image, pixel_scale, max_vis, dtype="c64", work_grids=True):
         import torch
         self.dtype_code = LMG_C64 if dtype == "c64" else LMG_C128
         self.cdtype = torch.complex64 if self.dtype_code == LMG_C64 else torch.complex128
         self.rdtype = torch.float32 if self.dtype_code == LMG_C64 else torch.float64
         h = ctypes.c_void_p()
-        _check(lib().lmg_plan_create(table._h, n_image, pixel_scale, max_vis, self.dtype_code, ctypes.byref(h)))
+        if work_grids:
+            _check(lib().lmg_plan_create(table._h, n_image, pixel_scale, max_vis, self.dtype_code, ctypes.byref(h)))
+        else:
+            _check(lib().lmg_plan_create_ex(table._h, n_image, pixel_scale, max_vis, self.dtype_code,
+                                            PLAN_NO_WORK_GRIDS, ctypes.byref(h)))
         self._h = h
         self.table = table
         self.n_image = n_image
@@ -236,6 +249,41 @@ class Plan:
         _check(lib().lmg_predict_vis(self._h, _ptr(image), _ptr(out), _stream()))
         return out
 
+    def workspace_bytes(self):
+        return int(lib().lmg_workspace_bytes(self._h))
+
+    def workspace(self, device=None):
+        """A device workspace for dirty_image / predict_vis with ws= (torch allocations are
+        256-byte aligned)."""
+        import torch
+        return torch.empty(self.workspace_bytes(), dtype=torch.uint8, device=device or "cuda")
+
+    def dirty_image_ws(self, vis, ws, weights=None, accum="plain", out=None):
+        import torch
+        vis, weights = self._vis_args(vis, weights)
+        if out is None:
+            out = torch.empty((self.n_image, self.n_image), dtype=self.cdtype, device=vis.device)
+        _need(out, self.cdtype, (self.n_image, self.n_image), "image")
+        _check(lib().lmg_dirty_image_ws(self._h, _ptr(vis), _ptr(weights), ACCUM[accum], _ptr(out), _ptr(ws),
+                                        ws.numel() * ws.element_size(), _stream()))
+        return out
+
+    def predict_vis_ws(self, image, ws, out=None):
+        import torch
+        _need(image, self.cdtype, (self.n_image, self.n_image), "image")
+        if out is None:
+            out = torch.empty(self.nvis, dtype=self.cdtype, device=image.device)
+        _need(out, self.cdtype, (self.nvis,), "vis_out")
+        _check(lib().lmg_predict_vis_ws(self._h, _ptr(image), _ptr(out), _ptr(ws), ws.numel() * ws.element_size(),
+                                        _stream()))
+        return out
+
+    def status(self):
+        """(rc, status bits) of lmg_plan_status: rc 0 or LMG_EDEVICE (-7)."""
+        bits = ctypes.c_int()
+        rc = lib().lmg_plan_status(self._h, ctypes.byref(bits), _stream())
+        return rc, bits.value
+
     def dropped(self):
         n = ctypes.c_int64()
         _check(lib().lmg_plan_dropped(self._h, ctypes.byref(n), _stream()))
@@ -254,6 +302,26 @@ class Plan:
         if getattr(self, "_h", None) and _lib is not None:
             _lib.lmg_plan_free(self._h)
             self._h = None
+
+
+def correct_factors(direction, inp, h, n_image, N, out=None):
+    """lmg_correct_factors: crop ("crop") or pad ("pad") with caller device factors h."""
+    import torch
+    cd = inp.dtype
+    dt = LMG_C64 if cd == torch.complex64 else LMG_C128
+    shape = (n_image, n_image) if direction == "crop" else (N, N)
+    if out is None:
+        out = torch.empty(shape, dtype=cd, device=inp.device)
+    _check(lib().lmg_correct_factors(LMG_CROP if direction == "crop" else LMG_PAD, _ptr(inp), _ptr(out), _ptr(h),
+                                     n_image, N, dt, _stream()))
+    return out
+
+
+def fp32_fma_rate():
+    """Measured float32 FMA throughput of the current device (flop/s); synchronises."""
+    r = ctypes.c_double()
+    _check(lib().lmg_fp32_fma_rate(ctypes.byref(r), _stream()))
+    return r.value
 
 
 STATIC_MAX_VIS = 262144

@@ -173,3 +173,53 @@ def test_direct_calculation_tables(lmg):
     assert np.abs(hd - hc).max() < 1e-12 * np.abs(hc).max()
     with pytest.raises(lmg.LmgError, match="lmg_kernel_table"):
         lmg.Table(4, 0.5, 64, "direct", values=np.ones((65, 4)))
+
+
+# ----------------------------------------------------------------------------------------
+# host-side fault injection (LMG_INJECT_FAULT) and the argument checks of the workspace,
+# factor-form correction and status calls; none of these reaches a kernel
+# ----------------------------------------------------------------------------------------
+def test_injected_host_allocation_failure(lmg, monkeypatch):
+    monkeypatch.setenv("LMG_INJECT_FAULT", "host_alloc")
+    L = lmg.lib()
+    h = ctypes.c_void_p()
+    assert L.lmg_kernel_table(5, 0.5, 100, 1, 0, ctypes.byref(h)) == -2 and not h.value
+    assert "host allocation" in L.lmg_last_error().decode()
+    vals = np.ones((101, 5))
+    assert L.lmg_table_from_values(5, 0.5, 100, 1, 0, vals.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)) == -2
+    monkeypatch.delenv("LMG_INJECT_FAULT")
+    assert L.lmg_kernel_table(5, 0.5, 100, 1, 0, ctypes.byref(h)) == 0 and h.value
+    L.lmg_table_free(h)
+
+
+@pytest.mark.parametrize("flags", [0, 1])
+def test_injected_device_allocation_failure(lmg, monkeypatch, flags):
+    """The first device allocation of a plan fails (before any CUDA call of the plan): the
+    plan is released and LMG_ENOMEM returned with the failing buffer named."""
+    t = lmg.Table(5, 0.5, 100, "linear")
+    monkeypatch.setenv("LMG_INJECT_FAULT", "device_alloc")
+    h = ctypes.c_void_p()
+    rc = lmg.lib().lmg_plan_create_ex(t._h, 64, 1e-3, 100, 0, flags, ctypes.byref(h))
+    assert rc == -2 and not h.value
+    msg = lmg.lib().lmg_last_error().decode()
+    assert "device allocation of table failed: injected" in msg
+
+
+def test_new_entry_point_argument_errors(lmg):
+    L = lmg.lib()
+    t = lmg.Table(5, 0.5, 100, "linear")
+    h = ctypes.c_void_p()
+    assert L.lmg_plan_create_ex(t._h, 64, 1e-3, 100, 0, 2, ctypes.byref(h)) == -1
+    assert "flags" in L.lmg_last_error().decode()
+    assert L.lmg_workspace_bytes(None) == 0
+    assert L.lmg_dirty_image_ws(None, None, None, 0, None, None, 0, None) == -1
+    assert L.lmg_predict_vis_ws(None, None, None, None, 0, None) == -1
+    assert L.lmg_plan_status(None, None, None) == -1
+    assert L.lmg_fp32_fma_rate(None, None) == -1
+    p16 = ctypes.c_void_p(256)
+    assert L.lmg_correct_factors(0, None, p16, p16, 64, 128, 0, None) == -1
+    assert L.lmg_correct_factors(0, p16, p16, p16, 63, 128, 0, None) == -1
+    assert L.lmg_correct_factors(0, p16, p16, p16, 64, 32, 0, None) == -1
+    assert L.lmg_correct_factors(0, p16, p16, p16, 64, 128, 2, None) == -1
+    assert L.lmg_correct_factors(2, p16, p16, p16, 64, 128, 0, None) == -1
+    assert "direction" in L.lmg_last_error().decode()

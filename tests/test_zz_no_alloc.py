@@ -53,3 +53,39 @@ def test_static_grid_rejects_sizes_beyond_its_limits():
     fine = lmg.Table(7, 0.5, 8192, "linear")
     with pytest.raises(lmg.LmgError, match="lmg_grid_static"):
         lmg.grid_static(fine, 512, 1.0 / 1024, uv, vis)
+
+
+def test_static_grid_allocates_no_device_memory():
+    """After a first call has set the device up, further calls leave the device's free
+    memory exactly where it was: the entry point's whole purpose."""
+    N, n_img = 1024, 512
+    tab = lmg.Table(7, 0.5, 1000, "linear")
+    uv, vis, w = _inputs(6, 50000, N)
+    out = torch.empty((N, N), dtype=torch.complex64, device="cuda")
+    lmg.grid_static(tab, n_img, 1.0 / N, uv, vis, w, out=out)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        lmg.grid_static(tab, n_img, 1.0 / N, uv, vis, w, out=out)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+
+
+@pytest.mark.parametrize("W,Ms,interp,N,nvis", [(7, 100, "cubic", 1024, 60000), (6, 200, "quadratic", 512, 30000),
+                                                (16, 1000, "linear", lmg.STATIC_MAX_N, lmg.STATIC_MAX_VIS),
+                                                (7, 1000, "linear", 1024, 0)])
+def test_static_grid_other_lookups_sizes_and_empty_input(W, Ms, interp, N, nvis):
+    """The extended-lookup sweeps (quadratic, cubic), the sized maxima (W = 16, N and nvis at
+    their limits) and an empty input, each against the allocating path."""
+    n_img = N // 2
+    tab = lmg.Table(W, 0.5, Ms, interp)
+    plan = lmg.Plan(tab, n_img, 1.0 / N, max(nvis, 1), "c64")
+    uv, vis, w = _inputs(7 + W, nvis, N)
+    ref = plan.bin(uv).grid(vis, w).cpu().numpy()
+    out = lmg.grid_static(tab, n_img, 1.0 / N, uv, vis, w).cpu().numpy()
+    if nvis == 0:
+        assert not np.any(out) and not np.any(ref)
+        return
+    scale = np.abs(ref).max()
+    assert np.abs(out - ref).max() <= 1e-5 * scale
+    assert np.sqrt(np.mean(np.abs(out - ref) ** 2)) <= 1e-6 * np.sqrt(np.mean(np.abs(ref) ** 2))
