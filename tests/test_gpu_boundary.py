@@ -63,7 +63,8 @@ def test_plan_without_work_grids(case):
     with pytest.raises(lmg.LmgError, match="lmg_predict_vis_ws"):
         p_lean.predict_vis(model)
     ws = p_lean.workspace()
-    assert torch.equal(p_lean.dirty_image_ws(visd, ws), p_full.dirty_image(visd))
+    # two plans bin in their own (atomic) record order: float32 sums agree to rounding
+    assert rel_rms(p_lean.dirty_image_ws(visd, ws).cpu().numpy(), p_full.dirty_image(visd).cpu().numpy()) < 1e-6
     assert rel_rms(p_lean.predict_vis_ws(model, ws).cpu().numpy(), p_full.predict_vis(model).cpu().numpy()) < 1e-6
 
 
