@@ -111,6 +111,7 @@ SweepArgs sweep_args(const lmg_plan* p) {
   a.interp = p->interp;
   a.N = static_cast<int>(p->N);
   a.n_strips = p->n_strips;
+  a.strip = p->strip;
   a.W = p->W;
   a.dtype = p->dtype;
   a.item_cap = p->item_cap;
@@ -242,8 +243,10 @@ int plan_create(const lmg_table* t, int64_t n_image, double pixel_scale, int64_t
   const int64_t N = int64_t(std::llround(Nd));
   if (std::fabs(Nd - double(N)) > 1e-9 * Nd || (N & 1))
     return set_error(LMG_EINVAL, "n_image / x0 must be an even integer");
-  if (N < 64 || N % kStrip != 0 || N > 65536)
-    return set_error(LMG_EINVAL, "grid size N = n_image / x0 must be a multiple of 32 in [64, 65536]");
+  const int strip = strip_width(dtype);
+  if (N < 64 || N % strip != 0 || N > 65536)
+    return set_error(LMG_EINVAL, "grid size N = n_image / x0 must be a multiple of " + std::to_string(strip) +
+                                     " (the strip width of this dtype) in [64, 65536]");
   if (N < 2 * t->W) return set_error(LMG_EINVAL, "grid too small for the support width");
 
   lmg_plan* p = new (std::nothrow) lmg_plan;
@@ -258,9 +261,10 @@ int plan_create(const lmg_table* t, int64_t n_image, double pixel_scale, int64_t
   p->pixel_scale = pixel_scale;
   p->scale2 = double(N) * pixel_scale * 4294967296.0;
   p->max_vis = max_vis;
-  p->n_strips = int(N / kStrip);
+  p->strip = strip;
+  p->n_strips = int(N / strip);
   const size_t rs = dtype == LMG_C128 ? 8 : 4;
-  p->Wp = dtype == LMG_C128 ? ((p->W + 1) & ~1) : (p->W | 1);
+  p->Wp = table_stride(p->W, dtype);
   const int nblk = int((N + opt.min_rows_per_block - 1) / opt.min_rows_per_block);
   p->item_cap = p->n_strips * nblk + int((2 * max_vis) / opt.min_item_target) + 2;
   if (inject_fault("item_cap")) p->item_cap = 1;
@@ -307,7 +311,7 @@ int plan_create(const lmg_table* t, int64_t n_image, double pixel_scale, int64_t
       (rc = dalloc(&p->offsets, size_t(L) + 1, "offsets")) || (rc = dalloc(&p->rank, size_t(max_vis), "ranks")) ||
       (rc = dalloc(&p->partial, size_t(p->nchunks), "scan")) || (rc = dalloc(&p->recs, size_t(2 * max_vis), "records")) ||
       (rc = dalloc(&p->items, size_t(p->item_cap), "items")) || (rc = dalloc(&p->counters, kNumCounters, "counters")) ||
-      (rc = dalloc(reinterpret_cast<unsigned char**>(&p->spill), size_t(p->item_cap) * ring_slots(p->W) * kStrip * c2, "spill")) ||
+      (rc = dalloc(reinterpret_cast<unsigned char**>(&p->spill), size_t(p->item_cap) * ring_slots(p->W) * strip * c2, "spill")) ||
       (opt.work_grid && (rc = dalloc(reinterpret_cast<unsigned char**>(&p->work), size_t(N) * size_t(N) * c2, "work grid"))) ||
       (opt.work_grid && (rc = dalloc(reinterpret_cast<unsigned char**>(&p->model), size_t(N) * size_t(N) * c2, "model grid")))) {
     free_plan(p);
@@ -393,6 +397,7 @@ int plan_bin(lmg_plan* p, const double* uv, int64_t nvis, cudaStream_t st) {
   a.W = p->W;
   a.N = int(p->N);
   a.n_strips = p->n_strips;
+  a.strip = p->strip;
   a.rows_per_block = p->rows_per_block;
   a.item_target = p->item_target;
   a.item_cap = p->item_cap;

@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks<W, float>())
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   unsigned char* my = batch_stage(smem, prefix, n_chan, tables, tab_floats, tab_in_smem,
-                                  align16(Stage<W, float>::grid_bytes));
+                                  Lay<W, float>::grid_bytes);
   const int* s_prefix = reinterpret_cast<const int*>(smem);
   const float* s_tab = reinterpret_cast<const float*>(smem + align16(sizeof(int) * size_t(n_chan + 1)));
   const int total = s_prefix[n_chan];
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks<W, float>())
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   unsigned char* my = batch_stage(smem, prefix, n_chan, tables, tab_floats, tab_in_smem,
-                                  align16(Stage<W, float>::degrid_bytes));
+                                  Lay<W, float>::degrid_bytes);
   const int* s_prefix = reinterpret_cast<const int*>(smem);
   const float* s_tab = reinterpret_cast<const float*>(smem + align16(sizeof(int) * size_t(n_chan + 1)));
   const int total = s_prefix[n_chan];
@@ -148,7 +148,7 @@ __global__ void k_batch_spill(const BatchChan* __restrict__ ch) {
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   for (int w = gw; w < total; w += (gridDim.x * blockDim.x) >> 5)
-    spill_item<float>(a.items, nfront, a.item_cap, a.W, RS, a.N, static_cast<const float2*>(a.spill),
+    spill_item<float>(a.items, nfront, a.item_cap, a.W, RS, a.N, a.strip, static_cast<const float2*>(a.spill),
                       static_cast<float2*>(a.grid), w, lane);
 }
 

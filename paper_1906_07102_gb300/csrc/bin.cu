@@ -1,4 +1,5 @@
-// Binning of visibility positions (support rule of Eq. 6) into 32-column strips sorted
+// Binning of visibility positions (support rule of Eq. 6) into strips of 64 (complex64) or
+// 32 (complex128) columns sorted
 // by pairs of support-start rows, and balanced work items for the sweep kernels.
 //
 // Pipeline (all on one stream, no host synchronisation):
@@ -44,7 +45,7 @@ __device__ __forceinline__ bool vis_position(double2 p, double scale2, int W, in
 constexpr int kCountIlp = 4;
 
 __global__ void k_bin_count(const double* __restrict__ uv, long long nvis, double scale2, int W,
-                            int N, int n_strips, int2* __restrict__ rank, int* __restrict__ hist,
+                            int N, int n_strips, int strip_w, int2* __restrict__ rank, int* __restrict__ hist,
                             int* __restrict__ counters) {
   const int lane = threadIdx.x & 31;  // for the dropped-position count
   const long long span = static_cast<long long>(blockDim.x) * kCountIlp;
@@ -61,9 +62,9 @@ __global__ void k_bin_count(const double* __restrict__ uv, long long nvis, doubl
       vp[u] = VisPos{-1, 0, 0u, 0u};
       if (k < nvis) {
         if (vis_position(reinterpret_cast<const double2*>(uv)[k], scale2, W, N, vp[u])) {
-          const int strip = vp[u].x0 / kStrip;
+          const int strip = vp[u].x0 / strip_w;
           key1[u] = strip * N + vp[u].y0;
-          if ((vp[u].x0 % kStrip) + W > kStrip) key2[u] = ((strip + 1) % n_strips) * N + vp[u].y0;
+          if ((vp[u].x0 % strip_w) + W > strip_w) key2[u] = ((strip + 1) % n_strips) * N + vp[u].y0;
         } else {
           bad[u] = true;
         }
@@ -188,8 +189,8 @@ __device__ __forceinline__ int dealt_position(int rho, int n) {
 }
 
 __global__ void k_bin_scatter(const double* __restrict__ uv, double scale2, const int2* __restrict__ rank,
-                              long long nvis, int W, int N, int n_strips, const int* __restrict__ offsets,
-                              Rec* __restrict__ recs) {
+                              long long nvis, int W, int N, int n_strips, int strip_w,
+                              const int* __restrict__ offsets, Rec* __restrict__ recs) {
   // kCountIlp visibilities per thread per iteration: their position, rank and offset loads
   // are in flight together (the pass is bound by its random L2 requests and their latency).
   // (u, v) and the ranks are read for the last time here: streaming loads (evict first)
@@ -214,10 +215,10 @@ __global__ void k_bin_scatter(const double* __restrict__ uv, double scale2, cons
     for (int u = 0; u < kCountIlp; ++u) {
       g1[u] = g2[u] = -1;
       if (vp[u].x0 >= 0) {
-        const int strip = vp[u].x0 / kStrip, xr = vp[u].x0 % kStrip;
+        const int strip = vp[u].x0 / strip_w, xr = vp[u].x0 % strip_w;
         const int pair_row = vp[u].y0 & ~1;
         g1[u] = strip * N + pair_row;
-        if (xr + W > kStrip) g2[u] = ((strip + 1) % n_strips) * N + pair_row;
+        if (xr + W > strip_w) g2[u] = ((strip + 1) % n_strips) * N + pair_row;
       }
     }
     int o1[kCountIlp][3], o2[kCountIlp][3];
@@ -233,13 +234,13 @@ __global__ void k_bin_scatter(const double* __restrict__ uv, double scale2, cons
     for (int u = 0; u < kCountIlp; ++u) {
       if (g1[u] < 0) continue;
       const long long k = base + u * blockDim.x + threadIdx.x;
-      const int odd = vp[u].y0 & 1, xr = vp[u].x0 % kStrip;
+      const int odd = vp[u].y0 & 1, xr = vp[u].x0 % strip_w;
       // row pair (y0 & ~1, y0 | 1) of the strip: [offsets[g], offsets[g + 2])
       recs[o1[u][0] + dealt_position((odd ? o1[u][1] - o1[u][0] : 0) + rk[u].x, o1[u][2] - o1[u][0])] =
           Rec{static_cast<unsigned>(k), rec_pack(vp[u].y0, xr), vp[u].su, vp[u].sv};
       if (g2[u] >= 0)
         recs[o2[u][0] + dealt_position((odd ? o2[u][1] - o2[u][0] : 0) + rk[u].y, o2[u][2] - o2[u][0])] =
-            Rec{static_cast<unsigned>(k), rec_pack(vp[u].y0, xr - kStrip), vp[u].su, vp[u].sv};
+            Rec{static_cast<unsigned>(k), rec_pack(vp[u].y0, xr - strip_w), vp[u].su, vp[u].sv};
     }
   }
 }
@@ -296,14 +297,14 @@ int bin_launch(const BinArgs& a, cudaStream_t st) {
   const int threads = 256;
   const long long want_c = (a.nvis + threads * kCountIlp - 1) / (threads * kCountIlp);
   const int blocks_c = static_cast<int>(want_c < a.max_blocks ? (want_c > 0 ? want_c : 1) : a.max_blocks);
-  k_bin_count<<<blocks_c, threads, 0, st>>>(a.uv, a.nvis, a.scale2, a.W, a.N, a.n_strips, a.rank, a.hist,
-                                          a.counters);
+  k_bin_count<<<blocks_c, threads, 0, st>>>(a.uv, a.nvis, a.scale2, a.W, a.N, a.n_strips, a.strip, a.rank,
+                                          a.hist, a.counters);
   const int nchunks = static_cast<int>((L + kScanChunk - 1) / kScanChunk);
   k_scan_partials<<<nchunks, kScanThreads, 0, st>>>(a.hist, L, a.partial);
   k_scan_top<<<1, 1024, 0, st>>>(a.partial, nchunks);
   k_scan_final<<<nchunks, kScanThreads, 0, st>>>(a.hist, L, a.partial, a.offsets);
-  k_bin_scatter<<<blocks_c, threads, 0, st>>>(a.uv, a.scale2, a.rank, a.nvis, a.W, a.N, a.n_strips, a.offsets,
-                                            a.recs);
+  k_bin_scatter<<<blocks_c, threads, 0, st>>>(a.uv, a.scale2, a.rank, a.nvis, a.W, a.N, a.n_strips, a.strip,
+                                            a.offsets, a.recs);
   const int nblk = (a.N + a.rows_per_block - 1) / a.rows_per_block;
   const int ntask = a.n_strips * nblk;
   if (a.rows_per_block > kMaxRowsPerBlock) return -1;

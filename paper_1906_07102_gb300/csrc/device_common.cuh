@@ -6,8 +6,6 @@
 
 namespace lmg {
 
-// Strip width: one warp lane per grid column.
-constexpr int kStrip = 32;
 constexpr int kFracBits = 32;
 
 // Support start (grid indices, wrapped to [0, N)) and fixed-point table coordinate of
@@ -17,9 +15,9 @@ struct VisPos {
   unsigned su, sv;
 };
 
-// One binned record: a visibility as seen from one 32-column strip. rx packs the
-// support-start row (bits 8..31) and xrel (bits 0..7, signed), the support start column
-// relative to the strip's first column (negative when the support started in the
+// One binned record: a visibility as seen from one strip (strip_width columns). rx packs
+// the support-start row (bits 8..31) and xrel (bits 0..7, signed), the support start
+// column relative to the strip's first column (negative when the support started in the
 // previous strip, i.e. for the strip's secondary copy).
 struct Rec {
   unsigned idx;
@@ -92,13 +90,6 @@ __device__ __forceinline__ unsigned transpose32(unsigned x, int lane) {
     else          x = (x & m) | ((y & m) << j);
   }
   return x;
-}
-
-// Lanes [xrel, xrel + W) intersected with [0, 32).
-__device__ __forceinline__ unsigned cover_mask(int xrel, int W) {
-  const unsigned long long full = (1ull << W) - 1ull;
-  const unsigned long long m = xrel >= 0 ? (full << xrel) : (full >> (-xrel));
-  return static_cast<unsigned>(m);
 }
 
 // Packed single-precision pairs (re, im) in one 64-bit register: Blackwell's f32x2 FMA

@@ -9,6 +9,17 @@ namespace lmg {
 // Nodes k = 0..Ng of the direct calculation's folded sums (Ng = 32, Appendix A).
 constexpr int kDirectNodes = 33;
 
+// Strip width of the binning and the sweeps: one lane per two columns for complex64 (64),
+// one lane per column for complex128 (32). dtype 0 = complex64, 1 = complex128.
+__host__ __device__ constexpr int strip_width(int dtype) { return dtype ? 32 : 64; }
+
+// Row stride (reals) of a device table: rows start on 16-byte boundaries and take an odd
+// number of 16-byte units, so that 16-byte loads of random rows spread over the banks;
+// entries W .. stride - 1 are zero.
+__host__ __device__ constexpr int table_stride(int W, int dtype) {
+  return ((((W * (dtype ? 8 : 4) + 15) / 16) | 1) * 16) / (dtype ? 8 : 4);
+}
+
 struct Rec;
 struct Item;
 
@@ -32,7 +43,7 @@ struct BinArgs {
   const double* uv;
   long long nvis;
   double scale2;  // N * pixel_scale * 2^32
-  int W, N, n_strips;
+  int W, N, n_strips, strip;  // strip: columns per strip (strip_width)
   int rows_per_block, item_target, item_cap;
   int max_blocks;
   int* hist;       // n_strips * N
@@ -54,7 +65,7 @@ struct SweepArgs {
   int* counters;
   const void* table;  // device, (Ms+1) x Wp of the plan's real type
   int Wp, Ms, interp;
-  int N, n_strips;
+  int N, n_strips, strip;
   int W;
   int dtype;          // 0 float, 1 double
   int accum;          // 0 plain, 1 compensated (float only)
@@ -66,7 +77,7 @@ struct SweepArgs {
   const void* vis;
   const void* weights;
   void* grid;
-  void* spill;        // item_cap * W * 32 complex
+  void* spill;        // item_cap * ring rows * strip complex
   // degridding
   const void* grid_in;
   void* vis_out;

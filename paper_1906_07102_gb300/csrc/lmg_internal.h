@@ -62,7 +62,7 @@ struct lmg_plan {
   double x0 = 0, pixel_scale = 0, scale2 = 0;
   // work items: blocks of 64 rows of a strip cut into items of ~512 records (measured best of
   // {64..512} x {256..2048} on the 4.1M-visibility tracks: better balance of the persistent sweeps)
-  int n_strips = 0, rows_per_block = 64, item_target = 512, item_cap = 0, nchunks = 0;
+  int n_strips = 0, strip = 64, rows_per_block = 64, item_target = 512, item_cap = 0, nchunks = 0;
   int64_t max_vis = 0, nvis = -1;
   int device = 0, sms = 0;
   int blocks_grid = 0, blocks_degrid = 0;

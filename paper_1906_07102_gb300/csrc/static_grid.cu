@@ -26,11 +26,12 @@ constexpr int kMaxN = LMG_STATIC_MAX_N;
 constexpr int kMaxOversample = LMG_STATIC_MAX_OVERSAMPLE;
 constexpr int kRowsPerBlock = 256;
 constexpr int kItemTarget = 1024;
-constexpr int kMaxStrips = kMaxN / kStrip;
+constexpr int kStaticStrip = strip_width(LMG_C64);  // complex64 only
+constexpr int kMaxStrips = kMaxN / kStaticStrip;
 constexpr long long kMaxBuckets = static_cast<long long>(kMaxStrips) * kMaxN;
 constexpr int kMaxItems = kMaxStrips * ((kMaxN + kRowsPerBlock - 1) / kRowsPerBlock) +
                           static_cast<int>((2 * kMaxVis) / kItemTarget) + 2;
-constexpr int kMaxWp = 17;      // float row stride W | 1 (odd), W <= 16
+constexpr int kMaxWp = table_stride(16, LMG_C64);  // float row stride for W <= 16
 constexpr int kMaxRing = 18;    // ring slots for W = 16
 
 constexpr size_t up256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -45,7 +46,7 @@ constexpr size_t kOffRecs = kOffPartial + up256(sizeof(int) * (kMaxBuckets / 409
 constexpr size_t kOffItems = kOffRecs + up256(sizeof(Rec) * 2 * kMaxVis);
 constexpr size_t kOffCounters = kOffItems + up256(sizeof(Item) * kMaxItems);
 constexpr size_t kOffSpill = kOffCounters + up256(sizeof(int) * kNumCounters);
-constexpr size_t kScratchBytes = kOffSpill + up256(sizeof(float2) * kMaxItems * kMaxRing * kStrip);
+constexpr size_t kScratchBytes = kOffSpill + up256(sizeof(float2) * kMaxItems * kMaxRing * kStaticStrip);
 
 // The working memory: allocated when the library is loaded, on every device that loads
 // it, and held until the process exits.
@@ -126,8 +127,8 @@ extern "C" int lmg_grid_static(const lmg_table* t, int64_t n_image, double pixel
   const double Nd = double(n_image) / t->x0;
   const int64_t N = int64_t(std::llround(Nd));
   if (std::fabs(Nd - double(N)) > 1e-9 * Nd || (N & 1)) return set_error(LMG_EINVAL, "n_image / x0 must be an even integer");
-  if (N < 64 || N % kStrip != 0 || N > kMaxN)
-    return set_error(LMG_EINVAL, "grid size N = n_image / x0 must be a multiple of 32 in [64, " +
+  if (N < 64 || N % kStaticStrip != 0 || N > kMaxN)
+    return set_error(LMG_EINVAL, "grid size N = n_image / x0 must be a multiple of 64 in [64, " +
                                      std::to_string(kMaxN) + "] for lmg_grid_static");
   if (N < 2 * t->W) return set_error(LMG_EINVAL, "grid too small for the support width");
 
@@ -139,7 +140,7 @@ extern "C" int lmg_grid_static(const lmg_table* t, int64_t n_image, double pixel
   if (int rc = setup_device(dev, &s)) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   unsigned char* base = s->base;
-  const int W = t->W, Ms = t->Ms, Wp = W | 1;
+  const int W = t->W, Ms = t->Ms, Wp = table_stride(W, LMG_C64);
 
   // Table rows in float32, padded to Wp, into the scratch -- only when this device does not
   // already hold this table. The upload copies from pageable host memory, which a stream
@@ -168,7 +169,7 @@ extern "C" int lmg_grid_static(const lmg_table* t, int64_t n_image, double pixel
     }
   }
 
-  const int n_strips = int(N / kStrip);
+  const int n_strips = int(N / kStaticStrip);
   const int nblk = int((N + kRowsPerBlock - 1) / kRowsPerBlock);
   const int item_cap = n_strips * nblk + int((2 * nvis) / kItemTarget) + 2;
   BinArgs b{};
@@ -178,6 +179,7 @@ extern "C" int lmg_grid_static(const lmg_table* t, int64_t n_image, double pixel
   b.W = W;
   b.N = int(N);
   b.n_strips = n_strips;
+  b.strip = kStaticStrip;
   b.rows_per_block = kRowsPerBlock;
   b.item_target = kItemTarget;
   b.item_cap = item_cap;
@@ -211,6 +213,7 @@ extern "C" int lmg_grid_static(const lmg_table* t, int64_t n_image, double pixel
   a.interp = t->interp;
   a.N = int(N);
   a.n_strips = n_strips;
+  a.strip = kStaticStrip;
   a.W = W;
   a.dtype = LMG_C64;
   a.accum = 0;

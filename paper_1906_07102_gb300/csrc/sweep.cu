@@ -13,7 +13,8 @@ __global__ void k_grid_spill(const Item* __restrict__ items, const int* __restri
   int nfront;
   const int total = work_total(counters, item_cap, nfront);
   const int w = static_cast<int>((static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
-  if (w < total) spill_item<R>(items, nfront, item_cap, W, RS, N, spill, grid, w, threadIdx.x & 31);
+  if (w < total)
+    spill_item<R>(items, nfront, item_cap, W, RS, N, 32 * cols_per_lane<R>(), spill, grid, w, threadIdx.x & 31);
 }
 
 void* kernel_for(int W, int dtype, int accum, bool degrid, bool ext) {
@@ -26,7 +27,7 @@ int ring_slots(int W) { return kD * ((W + kD - 1 + kD - 1) / kD); }
 
 size_t sweep_smem_bytes(int W, int dtype, int Ms, bool table_in_smem, bool degrid, int warps) {
   const size_t rs = dtype ? 8 : 4;
-  const int Wp = dtype ? ((W + 1) & ~1) : (W | 1);
+  const int Wp = table_stride(W, dtype);
   const size_t tab = table_in_smem ? align16(size_t(Ms + 1) * Wp * rs) : 0;
   return tab + size_t(warps) * stage_bytes(W, dtype, degrid);
 }
@@ -47,8 +48,8 @@ int sweep_occupancy(int W, int dtype, int accum, size_t smem_bytes, bool degrid,
 
 int sweep_config(int W, int dtype, int Ms, bool degrid, size_t limit, bool* table_in_smem, int* warps) {
   const size_t rs = dtype ? 8 : 4;
-  const int Wp = dtype ? ((W + 1) & ~1) : (W | 1);
-  *table_in_smem = align16(size_t(Ms + 1) * Wp * rs) <= 64 * 1024;
+  const int Wp = table_stride(W, dtype);
+  *table_in_smem = align16(size_t(Ms + 1) * Wp * rs) <= 96 * 1024;
   for (int pass = 0; pass < 2; ++pass) {
     for (int w = kWarps; w >= 1; w >>= 1) {
       if (sweep_smem_bytes(W, dtype, Ms, *table_in_smem, degrid, w) <= limit) {

@@ -1,34 +1,35 @@
 // Gridding and degridding sweeps (Eqs. 5-6 and their transpose, Section 4): the per-item
-// device code shared by the single-plan kernels (sweep.cu) and the multi-channel
-// persistent kernels (batch.cu).
+// device code shared by the single-plan kernels (sweep.cu, sweep_ext.cu) and the
+// multi-channel persistent kernels (batch.cu).
 //
-// The grid is cut into 32-column strips; a warp owns one work item (a range of rows of
-// one strip) and lane t owns column t of the strip. The item's records come grouped by
-// pairs of support-start rows (dealt inside a pair by the binning, so that 32 consecutive
-// records spread over the pair's columns) and are visited in groups of kD = 2 rows, in
-// chunks of up to 32 records
-// (the records and visibilities of the next two chunks are already in flight):
-//   1. the chunk's 2W table weights per record (Section 5.1 lookup) are staged in shared
-//      memory: Cu_i w V (gridding) or Cu_i (degridding), and Cv_j shifted by the record's
-//      row offset d in the group, so that entry q of the staged vector weights target row
-//      q of the group (q < T = W + kD - 1). G lanes share a record and look up one entry
-//      each (a lane per record would read 32 random table rows per instruction, which
-//      serialises on shared-memory banks). The shifted vectors are stored entry-major
-//      with a row pitch of 32 + 32/G, so that lanes reading entry q of different records
-//      hit distinct banks and so do the G lanes storing one record's entries;
-//   2. each lane builds the set of records whose support covers its column (32x32 bit
-//      transpose of the per-record cover masks) and visits them;
-//   3. gridding: lane t holds a ring of RS >= T accumulators (rows of its column) in
-//      registers and adds Cv'_q (Cu_i w V) to ring slot (base + q) -- a compile-time
-//      index, the group loop being unrolled over one ring period. After a group its kD rows
-//      are final and are stored as whole rows (256-byte coalesced stores for complex64).
-//      The W-1 rows past the item go to a spill buffer and are added by k_grid_spill once
-//      all items have stored their rows.
-//      degridding: the ring holds grid rows of the lane's column; lane t forms
-//      sum_q Cv'_q G[row0 + q][t] for each covering record and stages it; lane l sums
-//      Cu_i times its record's W staged sums and adds the result to the zeroed output (a
-//      visibility whose support crosses a strip has two records, one per strip).
+// The grid is cut into strips of S = 32 KC columns; a warp owns one work item (a range of
+// rows of one strip) and lane t owns the KC adjacent columns KC t .. KC t + KC - 1 of the
+// strip (KC = 2 for complex64, 1 for complex128). The item's records come grouped by pairs
+// of support-start rows (dealt inside a pair by the binning, so that 32 consecutive records
+// spread over the pair's columns) and are visited in groups of kD = 2 rows, in chunks of up
+// to 32 records (the records and visibilities of the next two chunks already in flight):
+//   1. each record's own lane looks up its 2W table weights (Section 5.1) and stages them:
+//      Cv shifted by the record's row offset d in the group (entry q weights group row q,
+//      q < TP, the window T = W + kD - 1 rounded up to even and zero-padded), record-major
+//      so that a visiting lane reads it with 16-byte loads; and per covered lane one slot of
+//      KC column weights: Cu_i w V (gridding) or Cu_i (degridding). Slot (lane mod PS) of a
+//      record belongs to the lane that reads it, so no lane needs the record's start column;
+//   2. each lane builds the set of records whose support covers one of its columns (32x32
+//      bit transpose of the per-record lane masks) and visits them, two per iteration;
+//   3. gridding: lane t holds a ring of RS >= TP accumulator rows for each of its columns in
+//      registers, as pairs of rows (one f32x2 register per pair for complex64), and adds
+//      (Cv'_q, Cv'_q+1) x (a, a) with one packed FMA per pair and per real/imaginary part --
+//      the ring index is compile-time, the group loop being unrolled over one ring period.
+//      After a group its kD rows are final and stored as whole rows (512-byte coalesced
+//      stores for complex64). The W-1 rows past the item go to a spill buffer and are added
+//      by k_grid_spill once all items have stored their rows.
+//      degridding: the ring holds grid rows of the lane's columns; the lane forms
+//      sum_q Cv'_q G[row0 + q][c] for its columns, weights them by its Cu slot and stages the
+//      sum in the record's partial-sum slot; the record's lane adds its slots and adds the
+//      result to the zeroed output (a visibility whose support crosses a strip has two
+//      records, one per strip).
 // Every grid cell is written exactly once by the gridding sweep (no pre-zeroing, no
+// shared-memory atomics); only the spill rows are added with global vector atomics.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -44,43 +45,87 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
-template <typename R> __host__ __device__ constexpr int wpad(int W) {
-  return sizeof(R) == 4 ? (W | 1) : ((W + 1) & ~1);
-}
-
-// Rows per group and the register ring: RS >= T = W + kD - 1 slots, a multiple of kD, so
-// that the group loop unrolled over P = RS / kD groups indexes every slot at compile time.
+// Rows per group and the register ring: RS >= TP slots, a multiple of kD, so that the
+// group loop unrolled over P = RS / kD groups indexes every slot at compile time.
 constexpr int kD = 2;  // the binning's row pairs (bin.cu) are these groups
 template <int W> struct Ring {
-  static constexpr int T = W + kD - 1;
-  static constexpr int R = kD * ((T + kD - 1) / kD);
+  static constexpr int T = W + kD - 1;       // rows a group's records can touch
+  static constexpr int TP = 2 * ((T + 1) / 2);  // staged entries: T rounded up to pairs
+  static constexpr int R = kD * ((TP + kD - 1) / kD);
   static constexpr int P = R / kD;
 };
 
-// Cooperative table lookup while staging a chunk: G lanes share one record (each computes
-// one table entry), P = 32 / G records per round.
-template <int W> struct Coop {
-  static constexpr int G = W <= 4 ? 4 : (W <= 8 ? 8 : 16);
-  static constexpr int P = 32 / G;
-  // Row pitch (elements) of the staged Cv: entry q of record l sits at q * pitch + l. The
-  // extra P elements put the entries of the P records of one staging round in distinct
-  // banks, while the sweep's reads (entry q of different records) stay conflict-free.
-  static constexpr int pitch = 32 + P;
-};
-__host__ __device__ constexpr int coop_group(int W) { return W <= 4 ? 4 : (W <= 8 ? 8 : 16); }
-
 __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
-template <int W, typename R> struct Stage {
-  // per warp: x0[32] | cvs[T][pitch] (entry-major) | cu[32][W] (degrid) | a or p [32][W] complex
-  static constexpr int T = Ring<W>::T;
-  static constexpr size_t x0_bytes = 32 * sizeof(int);
-  static constexpr size_t cv_bytes = align16(size_t(T) * Coop<W>::pitch * sizeof(R));
-  static constexpr size_t cu_bytes = 32 * W * sizeof(R);
-  static constexpr size_t a_bytes = 32 * W * 2 * sizeof(R);
-  static constexpr size_t grid_bytes = x0_bytes + cv_bytes + a_bytes;
-  static constexpr size_t degrid_bytes = x0_bytes + cv_bytes + cu_bytes + a_bytes;
+// Columns per lane: 2 for complex64 (64-column strips), 1 for complex128 (32 columns).
+template <typename R> __host__ __device__ constexpr int cols_per_lane() { return sizeof(R) == 4 ? 2 : 1; }
+
+// Staging layout of one warp.
+template <int W, typename R> struct Lay {
+  static constexpr int KC = cols_per_lane<R>();
+  static constexpr int TP = Ring<W>::TP;
+  // Cv' record-major, CVS reals per record (an odd number of 16-byte units)
+  static constexpr int CVS = ((((TP * int(sizeof(R)) + 15) / 16) | 1) * 16) / int(sizeof(R));
+  // lanes one record can cover, and the slots per record (a power of two >= NL)
+  static constexpr int NL = (W - 1 + KC - 1) / KC + 1;
+  static constexpr int PS = NL <= 2 ? 2 : (NL <= 4 ? 4 : (NL <= 8 ? 8 : 16));
+  // slot sizes: KC complex (gridding a = Cu w V), KC reals (degridding Cu), one complex
+  // (degridding partial sum); each record holds PS + 1 slots (odd pitch: spreads banks)
+  static constexpr int SA = KC * 2 * int(sizeof(R));
+  static constexpr int SU = KC * int(sizeof(R));
+  static constexpr int SP = 2 * int(sizeof(R));
+  static constexpr size_t cv_bytes = size_t(32) * CVS * sizeof(R);
+  static constexpr size_t a_bytes = size_t(32) * (PS + 1) * SA;
+  static constexpr size_t u_bytes = size_t(32) * (PS + 1) * SU;
+  static constexpr size_t p_bytes = size_t(32) * (PS + 1) * SP;
+  static constexpr size_t grid_bytes = align16(cv_bytes + a_bytes);
+  static constexpr size_t degrid_bytes = align16(cv_bytes + align16(u_bytes) + p_bytes);
 };
+
+// Pairs of rows in one register: f32x2 for float (Blackwell's packed FMA), two doubles.
+template <typename R> struct PairOf;
+template <> struct PairOf<float> { using T = unsigned long long; };
+template <> struct PairOf<double> { using T = double2; };
+
+__device__ __forceinline__ unsigned long long pfma(unsigned long long a, unsigned long long b, unsigned long long c) {
+  return f2fma(a, b, c);
+}
+__device__ __forceinline__ double2 pfma(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ unsigned long long pdup(float x) { return f2pack(x, x); }
+__device__ __forceinline__ double2 pdup(double x) { return make_double2(x, x); }
+template <typename P> __device__ __forceinline__ P pzero();
+template <> __device__ __forceinline__ unsigned long long pzero<unsigned long long>() { return 0ull; }
+template <> __device__ __forceinline__ double2 pzero<double2>() { return make_double2(0.0, 0.0); }
+__device__ __forceinline__ float plo(unsigned long long p) { return f2unpack(p).x; }
+__device__ __forceinline__ float phi(unsigned long long p) { return f2unpack(p).y; }
+__device__ __forceinline__ double plo(double2 p) { return p.x; }
+__device__ __forceinline__ double phi(double2 p) { return p.y; }
+__device__ __forceinline__ float psum(unsigned long long p) {
+  const float2 v = f2unpack(p);
+  return v.x + v.y;
+}
+__device__ __forceinline__ double psum(double2 p) { return p.x + p.y; }
+
+// Packed error-free addition (Knuth TwoSum on both halves): a receives the rounded sum,
+// lo accumulates the rounding errors (compensated accumulation, complex64 only).
+__device__ __forceinline__ void two_sum_pair(unsigned long long& a, unsigned long long& lo, unsigned long long b) {
+  unsigned long long s, bp, ap, ea, eb;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(s) : "l"(a), "l"(b));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(bp) : "l"(s), "l"(a));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(ap) : "l"(s), "l"(bp));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(ea) : "l"(a), "l"(ap));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(eb) : "l"(b), "l"(bp));
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(ea) : "l"(ea), "l"(eb));
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(lo) : "l"(lo), "l"(ea));
+  a = s;
+}
+__device__ __forceinline__ unsigned long long pmul(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
 
 // Table lookup (Section 5.1, Appendix F): row offset (elements) and interpolation fraction
 // of coordinate S (units of 2^-32), from the exact integer product S Ms. Linear uses row
@@ -143,100 +188,171 @@ __device__ __forceinline__ R lagrange_entry(const R* __restrict__ p, int Wp, int
          sixth * a * b * c * p[3 * Wp];
 }
 
-// Stages the weights of a chunk's records, held one per lane by lanes lo .. hi-1 (table
-// row offsets and fractions for u and v, row offset d in the group, and for gridding
-// w V): Cv shifted by d into s_cv (entry q of record l at q * pitch + l, zero for q
-// outside [d, d + W)) and Cu, times w V when gridding, into s_u[l * W + i]. G lanes share
-// a record and compute one table entry each (C = T[k] + f (T[k+1] - T[k]), or Lagrange
-// through d + 1 rows), so a round's
-// table reads touch P rows instead of 32 rows per instruction.
-template <int W, typename R, bool GRID, bool EXT>
-__device__ __forceinline__ void stage_chunk(const R* __restrict__ tab, int Wp, int interp, int lo, int hi, int ou,
-                                            R fu, int ov, R fv, int d, R wx, R wy, R* __restrict__ s_cv,
-                                            void* __restrict__ s_u, int lane) {
-  using C2 = typename Cplx<R>::T;
-  constexpr int G = Coop<W>::G, P = Coop<W>::P, pitch = Coop<W>::pitch, TT = Ring<W>::T;
-  const int g = lane / G, i = lane % G;
-  const int ovd = ov | (d << 28);  // row offsets stay below 2^28 (Ms <= 10^6, Wp <= 16)
-  for (int r0 = lo; r0 < hi; r0 += P) {
-    const int r = r0 + g, src = r & 31;
-    const int ou_r = __shfl_sync(0xffffffffu, ou, src);
-    const R fu_r = __shfl_sync(0xffffffffu, fu, src);
-    const int ovd_r = __shfl_sync(0xffffffffu, ovd, src);
-    const R fv_r = __shfl_sync(0xffffffffu, fv, src);
-    const int ov_r = ovd_r & 0x0fffffff, d_r = ovd_r >> 28;
-    R wx_r = R(0), wy_r = R(0);
-    if constexpr (GRID) {
-      wx_r = __shfl_sync(0xffffffffu, wx, src);
-      wy_r = __shfl_sync(0xffffffffu, wy, src);
-    }
-    if (r < hi) {
-      if (i < W) {
-        R cu, cv;
-        if constexpr (!EXT) {
-          cu = tab[ou_r + i];
-          cv = tab[ov_r + i];
-          if (interp) {
-            cu = cu + fu_r * (tab[ou_r + Wp + i] - cu);
-            cv = cv + fv_r * (tab[ov_r + Wp + i] - cv);
-          }
-        } else {
-          // direct calculation exists for float64 plans and W <= 11 only (plan creation)
-          if constexpr (sizeof(R) == 8 && W <= 11) {
-            if (interp == 4) {
-              cu = direct_entry<R>(tab, W, i, fu_r);
-              cv = direct_entry<R>(tab, W, i, fv_r);
-            } else {
-              cu = lagrange_entry<R>(tab + ou_r + i, Wp, interp, fu_r);
-              cv = lagrange_entry<R>(tab + ov_r + i, Wp, interp, fv_r);
-            }
-          } else {
-            cu = lagrange_entry<R>(tab + ou_r + i, Wp, interp, fu_r);
-            cv = lagrange_entry<R>(tab + ov_r + i, Wp, interp, fv_r);
-          }
-        }
-        if constexpr (GRID) {
-          C2 t;
-          t.x = cu * wx_r;
-          t.y = cu * wy_r;
-          static_cast<C2*>(s_u)[r * W + i] = t;
-        } else {
-          static_cast<R*>(s_u)[r * W + i] = cu;
-        }
-        s_cv[(i + d_r) * pitch + r] = cv;
+// 16-byte vector of reals.
+template <typename R> struct Vec16;
+template <> struct Vec16<float> {
+  using T = float4;
+  static constexpr int N = 4;
+};
+template <> struct Vec16<double> {
+  using T = double2;
+  static constexpr int N = 2;
+};
+template <typename R> __device__ __forceinline__ R vget(const typename Vec16<R>::T& v, int k);
+template <> __device__ __forceinline__ float vget<float>(const float4& v, int k) {
+  return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+}
+template <> __device__ __forceinline__ double vget<double>(const double2& v, int k) { return k == 0 ? v.x : v.y; }
+
+// The W table weights at one coordinate (row offset `off`, fraction f): nearest / linear
+// rows read with 16-byte loads, or the extended lookups (Lagrange, direct calculation).
+template <int W, typename R, bool EXT>
+__device__ __forceinline__ void lookup(const R* __restrict__ tab, int Wp, int interp, int off, R f, R (&c)[W]) {
+  if constexpr (!EXT) {
+    using V = typename Vec16<R>::T;
+    constexpr int VE = Vec16<R>::N, NV = (W + VE - 1) / VE;
+    const V* p0 = reinterpret_cast<const V*>(tab + off);
+    V r0[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) r0[v] = p0[v];
+    if (interp) {
+      const V* p1 = reinterpret_cast<const V*>(tab + off + Wp);
+      V r1[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) r1[v] = p1[v];
+#pragma unroll
+      for (int i = 0; i < W; ++i) {
+        const R a = vget<R>(r0[i / VE], i % VE);
+        c[i] = a + f * (vget<R>(r1[i / VE], i % VE) - a);
       }
-      // the kD - 1 zero entries, on the group's spare lanes where it has them
-      for (int z = (i - W + G) % G; z < TT - W; z += G) s_cv[(z < d_r ? z : z + W) * pitch + r] = R(0);
+    } else {
+#pragma unroll
+      for (int i = 0; i < W; ++i) c[i] = vget<R>(r0[i / VE], i % VE);
+    }
+  } else {
+    // direct calculation exists for float64 plans and W <= 11 only (plan creation)
+    if constexpr (sizeof(R) == 8 && W <= 11) {
+      if (interp == 4) {
+#pragma unroll 1
+        for (int i = 0; i < W; ++i) c[i] = direct_entry<R>(tab, W, i, f);
+        return;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < W; ++i) c[i] = lagrange_entry<R>(tab + off + i, Wp, interp, f);
+  }
+}
+
+// Stages Cv' (Cv shifted by the row offset d in {0, 1}, zero outside) record-major at dst
+// (TP reals, 16-byte aligned), with 16-byte stores.
+template <int W, typename R>
+__device__ __forceinline__ void stage_cv(const R (&cv)[W], int d, R* __restrict__ dst) {
+  using V = typename Vec16<R>::T;
+  constexpr int TP = Ring<W>::TP, VE = Vec16<R>::N, NV = (TP + VE - 1) / VE;
+  R e[NV * VE];
+#pragma unroll
+  for (int q = 0; q < NV * VE; ++q) {
+    const R c0 = q < W ? cv[q] : R(0);            // d = 0: entry q is Cv_q
+    const R c1 = (q >= 1 && q <= W) ? cv[q - 1] : R(0);  // d = 1: entry q is Cv_{q-1}
+    e[q] = d ? c1 : c0;
+  }
+  V* out = reinterpret_cast<V*>(dst);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    V x;
+    if constexpr (sizeof(R) == 4) x = make_float4(e[4 * v], e[4 * v + 1], e[4 * v + 2], e[4 * v + 3]);
+    else x = make_double2(e[2 * v], e[2 * v + 1]);
+    out[v] = x;
+  }
+}
+
+// Column weights of record xrel (support start column relative to the strip) for covered
+// lane L0 + m: entry j < KC is the weight of column KC (L0 + m) + j, i.e. of support index
+// i = KC m + j - (xrel mod KC); zero outside [0, W).
+template <int W, int KC> __device__ __forceinline__ int slot_index(int m, int j, int par) { return KC * m + j - par; }
+
+// Gridding stage of a record by its own lane: Cv' and the slots a = Cu w V.
+template <int W, typename R, bool EXT>
+__device__ __forceinline__ void stage_grid(const R* __restrict__ tab, int Wp, int interp, int ou, R fu, int ov, R fv,
+                                           int d, int xrel, R wx, R wy, unsigned char* __restrict__ s_cv,
+                                           unsigned char* __restrict__ s_a, int lane) {
+  using L = Lay<W, R>;
+  constexpr int KC = L::KC;
+  R cu[W], cv[W];
+  lookup<W, R, EXT>(tab, Wp, interp, ou, fu, cu);
+  lookup<W, R, EXT>(tab, Wp, interp, ov, fv, cv);
+  stage_cv<W, R>(cv, d, reinterpret_cast<R*>(s_cv) + lane * L::CVS);
+  unsigned char* rec = s_a + lane * (L::PS + 1) * L::SA;
+  const int L0 = xrel >> (KC - 1), par = xrel & (KC - 1);
+#pragma unroll
+  for (int m = 0; m < L::NL; ++m) {
+    R v[2 * KC];
+#pragma unroll
+    for (int j = 0; j < KC; ++j) {
+      R re = R(0), im = R(0);
+#pragma unroll
+      for (int pp = 0; pp < KC; ++pp) {  // par is runtime: pick the support index by parity
+        const int i = slot_index<W, KC>(m, j, pp);
+        if (pp == par && i >= 0 && i < W) {
+          re = cu[i] * wx;
+          im = cu[i] * wy;
+        }
+      }
+      v[2 * j] = re;
+      v[2 * j + 1] = im;
+    }
+    unsigned char* dst = rec + ((L0 + m) & (L::PS - 1)) * L::SA;
+    if constexpr (sizeof(R) == 4 && KC == 2) {
+      *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+    } else if constexpr (sizeof(R) == 4) {
+      *reinterpret_cast<float2*>(dst) = make_float2(v[0], v[1]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < KC; ++j) reinterpret_cast<double2*>(dst)[j] = make_double2(v[2 * j], v[2 * j + 1]);
     }
   }
 }
 
-// Gridding staging by the record's own lane (nearest / linear): the lane reads its rows
-// with scalar loads. The float32 table rows have an odd stride (W | 1), so 32 random rows
-// spread over the banks; measured faster for gridding than the cooperative staging, which
-// degridding keeps (its staging is lighter).
-template <int W, typename R>
-__device__ __forceinline__ void stage_own(const R* __restrict__ tab, int Wp, int interp, bool mine, int ou, R fu,
-                                          int ov, R fv, int d, R wx, R wy, R* __restrict__ s_cv,
-                                          typename Cplx<R>::T* __restrict__ s_a, int lane) {
-  using C2 = typename Cplx<R>::T;
-  constexpr int pitch = Coop<W>::pitch, TT = Ring<W>::T;
-  if (!mine) return;
+// Degridding stage of a record by its own lane: Cv' and the slots of Cu.
+template <int W, typename R, bool EXT>
+__device__ __forceinline__ void stage_degrid(const R* __restrict__ tab, int Wp, int interp, int ou, R fu, int ov, R fv,
+                                             int d, int xrel, unsigned char* __restrict__ s_cv,
+                                             unsigned char* __restrict__ s_u, int lane) {
+  using L = Lay<W, R>;
+  constexpr int KC = L::KC;
+  R cu[W], cv[W];
+  lookup<W, R, EXT>(tab, Wp, interp, ou, fu, cu);
+  lookup<W, R, EXT>(tab, Wp, interp, ov, fv, cv);
+  stage_cv<W, R>(cv, d, reinterpret_cast<R*>(s_cv) + lane * L::CVS);
+  unsigned char* rec = s_u + lane * (L::PS + 1) * L::SU;
+  const int L0 = xrel >> (KC - 1), par = xrel & (KC - 1);
 #pragma unroll
-  for (int i = 0; i < W; ++i) {
-    R cu = tab[ou + i], cv = tab[ov + i];
-    if (interp) {
-      cu = cu + fu * (tab[ou + Wp + i] - cu);
-      cv = cv + fv * (tab[ov + Wp + i] - cv);
+  for (int m = 0; m < L::NL; ++m) {
+    R v[KC];
+#pragma unroll
+    for (int j = 0; j < KC; ++j) {
+      R c = R(0);
+#pragma unroll
+      for (int pp = 0; pp < KC; ++pp) {
+        const int i = slot_index<W, KC>(m, j, pp);
+        if (pp == par && i >= 0 && i < W) c = cu[i];
+      }
+      v[j] = c;
     }
-    C2 t;
-    t.x = cu * wx;
-    t.y = cu * wy;
-    s_a[lane * W + i] = t;
-    s_cv[(i + d) * pitch + lane] = cv;
+    unsigned char* dst = rec + ((L0 + m) & (L::PS - 1)) * L::SU;
+    if constexpr (sizeof(R) == 4 && KC == 2) *reinterpret_cast<float2*>(dst) = make_float2(v[0], v[1]);
+    else *reinterpret_cast<R*>(dst) = v[0];
   }
-#pragma unroll
-  for (int z = 0; z < TT - W; ++z) s_cv[(z < d ? z : z + W) * pitch + lane] = R(0);
+}
+
+// Lanes L0 .. L1 (inclusive) intersected with [0, 32).
+__device__ __forceinline__ unsigned lane_range_mask(int L0, int L1) {
+  const int a = L0 < 0 ? 0 : L0, b = L1 > 31 ? 31 : L1;
+  if (a > b) return 0u;
+  return (0xffffffffu >> (31 - b)) & (0xffffffffu << a);
+}
+template <int W, int KC> __device__ __forceinline__ unsigned cover_lanes(int xrel) {
+  return lane_range_mask(xrel >> (KC - 1), (xrel + W - 1) >> (KC - 1));
 }
 
 // Copy a table into shared memory (all threads of the CTA), or use it in place.
@@ -272,21 +388,66 @@ template <typename R> struct Fetch {
   R wt;
 };
 
-// Error-free addition s + e = a + b (Knuth TwoSum); a receives s, lo accumulates e.
-__device__ __forceinline__ void two_sum_acc(float& a, float& lo, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bp = __fsub_rn(s, a);
-  const float ap = __fsub_rn(s, bp);
-  lo += __fsub_rn(a, ap) + __fsub_rn(b, bp);
-  a = s;
-}
-
 // Resident CTAs per SM the register allocation must allow.
 template <int W, typename R, bool COMP = false, bool EXT = false> constexpr int min_blocks() {
-  // the extended lookups (Lagrange, direct) need more registers: fewer resident CTAs
-  return COMP ? 2 : ((sizeof(R) == 4 && W <= 8) ? (EXT ? 2 : 3) : 1);
+  return (sizeof(R) == 4 && W <= 8 && !COMP) ? 2 : 1;
 }
 
+// KC complex values of one row of a lane's columns: 16-byte store / load.
+template <typename R, int KC>
+__device__ __forceinline__ void store_cols(typename Cplx<R>::T* dst, const R (&re)[KC], const R (&im)[KC]) {
+  if constexpr (sizeof(R) == 4 && KC == 2) {
+    *reinterpret_cast<float4*>(dst) = make_float4(re[0], im[0], re[1], im[1]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < KC; ++j) {
+      typename Cplx<R>::T o;
+      o.x = re[j];
+      o.y = im[j];
+      dst[j] = o;
+    }
+  }
+}
+template <typename R, int KC>
+__device__ __forceinline__ void load_cols(const typename Cplx<R>::T* src, R (&re)[KC], R (&im)[KC]) {
+  if constexpr (sizeof(R) == 4 && KC == 2) {
+    const float4 v = *reinterpret_cast<const float4*>(src);
+    re[0] = v.x;
+    im[0] = v.y;
+    re[1] = v.z;
+    im[1] = v.w;
+  } else {
+#pragma unroll
+    for (int j = 0; j < KC; ++j) {
+      const typename Cplx<R>::T v = src[j];
+      re[j] = v.x;
+      im[j] = v.y;
+    }
+  }
+}
+
+// Loads the Cv' pairs of record l.
+template <int W, typename R>
+__device__ __forceinline__ void load_cv_pairs(const unsigned char* s_cv, int l,
+                                              typename PairOf<R>::T (&c)[Ring<W>::TP / 2]) {
+  using L = Lay<W, R>;
+  constexpr int NPR = Ring<W>::TP / 2;
+  const R* p = reinterpret_cast<const R*>(s_cv) + l * L::CVS;
+  if constexpr (sizeof(R) == 4) {
+    const ulonglong2* v = reinterpret_cast<const ulonglong2*>(p);
+#pragma unroll
+    for (int m = 0; m < NPR / 2; ++m) {
+      const ulonglong2 x = v[m];
+      c[2 * m] = x.x;
+      c[2 * m + 1] = x.y;
+    }
+    if constexpr (NPR % 2) c[NPR - 1] = reinterpret_cast<const unsigned long long*>(p)[NPR - 1];
+  } else {
+    const double2* v = reinterpret_cast<const double2*>(p);
+#pragma unroll
+    for (int m = 0; m < NPR; ++m) c[m] = v[m];
+  }
+}
 
 // One gridding work item (rows [r0, r1) of one strip), run by the 32 lanes of a warp;
 // `my` is the warp's staging area in shared memory, `tab` the table (shared or global).
@@ -294,19 +455,20 @@ template <int W, typename R, bool COMP, bool EXT = false>
 __device__ __forceinline__ void grid_item(const SweepArgs& a, const R* __restrict__ tab, unsigned char* my,
                                           int slot, int lane) {
   using C2 = typename Cplx<R>::T;
-  using St = Stage<W, R>;
-  constexpr int Wp = wpad<R>(W);
-  constexpr int RS = Ring<W>::R, P = Ring<W>::P, TT = Ring<W>::T;
-  int* s_x0 = reinterpret_cast<int*>(my);
-  R* s_cv = reinterpret_cast<R*>(my + St::x0_bytes);
-  C2* s_a = reinterpret_cast<C2*>(my + St::x0_bytes + St::cv_bytes);
+  using P = typename PairOf<R>::T;
+  using L = Lay<W, R>;
+  constexpr int KC = L::KC, S = 32 * KC;
+  constexpr int RS = Ring<W>::R, NP = Ring<W>::P, NPR = Ring<W>::TP / 2, RH = RS / 2;
+  static_assert(!COMP || sizeof(R) == 4, "compensated accumulation is for complex64");
+  unsigned char* s_cv = my;
+  unsigned char* s_a = my + L::cv_bytes;
 
   const Rec* __restrict__ recs = a.recs;
   const C2* __restrict__ vis = static_cast<const C2*>(a.vis);
   const R* __restrict__ wts = static_cast<const R*>(a.weights);
   C2* __restrict__ grid = static_cast<C2*>(a.grid);
   C2* __restrict__ spill = static_cast<C2*>(a.spill);
-  const int N = a.N;
+  const int N = a.N, Wp = a.Wp;
 
   auto fetch_rec = [&](int start, int end, Fetch<R>& f) {
     if (start + lane < end) f.rc = recs[start + lane];
@@ -320,15 +482,22 @@ __device__ __forceinline__ void grid_item(const SweepArgs& a, const R* __restric
 
   const Item item = a.items[slot];
   const int* __restrict__ off = a.offsets + static_cast<long long>(item.strip) * N;
-  const int col = item.strip * kStrip + lane;
+  const int col0 = item.strip * S + KC * lane;
   const int nrows = item.r1 - item.r0;
-  // ring slot x % RS accumulates relative row x of column `col` (separate real and
-  // imaginary arrays: two scalar FMAs measured faster here than one packed f32x2 FMA)
-  R acc_re[RS], acc_im[RS], lo_re[RS], lo_im[RS];
+  // ring pair h holds relative rows 2h' and 2h' + 1 (h' = h mod RH) of the lane's columns
+  P accR[KC][RH], accI[KC][RH];
+  P loR[COMP ? KC : 1][COMP ? RH : 1], loI[COMP ? KC : 1][COMP ? RH : 1];
 #pragma unroll
-  for (int q = 0; q < RS; ++q) {
-    acc_re[q] = acc_im[q] = lo_re[q] = lo_im[q] = R(0);
+  for (int j = 0; j < KC; ++j)
+#pragma unroll
+    for (int h = 0; h < RH; ++h) accR[j][h] = accI[j][h] = pzero<P>();
+  if constexpr (COMP) {
+#pragma unroll
+    for (int j = 0; j < KC; ++j)
+#pragma unroll
+      for (int h = 0; h < RH; ++h) loR[j][h] = loI[j][h] = pzero<P>();
   }
+  const int myslot = lane & (L::PS - 1);
   // software pipeline over 32-record windows of the item (window k = records
   // rb + 32k .. rb + 32k + 31, lane l holding record rb + 32k + l): while window k is
   // processed, the visibilities of window k+1 and the records of window k+2 are in flight
@@ -342,7 +511,7 @@ __device__ __forceinline__ void grid_item(const SweepArgs& a, const R* __restric
   fetch_rec(rb + 64, rend, f2);
   for (int g0 = 0; g0 < nrows; g0 += RS) {
 #pragma unroll
-    for (int gp = 0; gp < P; ++gp) {
+    for (int gp = 0; gp < NP; ++gp) {
       const int gb = g0 + gp * kD;
       if (gb < nrows) {
         const int row0 = item.r0 + gb;
@@ -350,57 +519,50 @@ __device__ __forceinline__ void grid_item(const SweepArgs& a, const R* __restric
         while (cstart < re) {
           // chunk: records [cstart, ce) of window wbase, staged by lanes cstart - wbase ..
           const int ce = min(re, wbase + 32);
-          const int lo = cstart - wbase, hi = ce - wbase;
-          const bool mine = lane >= lo && lane < hi;
+          const bool mine = lane >= cstart - wbase && lane < ce - wbase;
           const int xrel = rec_xrel(f0.rc.rx);
-          if (mine) s_x0[lane] = xrel;
-          int ou, ov;
-          R fu, fv;
-          table_coord<R, EXT>(Wp, a.Ms, a.interp, f0.rc.su, ou, fu);
-          table_coord<R, EXT>(Wp, a.Ms, a.interp, f0.rc.sv, ov, fv);
-          if constexpr (EXT)
-            stage_chunk<W, R, true, EXT>(tab, Wp, a.interp, lo, hi, ou, fu, ov, fv, rec_row(f0.rc.rx) - row0,
-                                         f0.v.x * f0.wt, f0.v.y * f0.wt, s_cv, s_a, lane);
-          else
-            stage_own<W, R>(tab, Wp, a.interp, mine, ou, fu, ov, fv, rec_row(f0.rc.rx) - row0, f0.v.x * f0.wt,
-                            f0.v.y * f0.wt, s_cv, s_a, lane);
-          const unsigned cover = mine ? cover_mask(xrel, W) : 0u;
+          if (mine) {
+            int ou, ov;
+            R fu, fv;
+            table_coord<R, EXT>(Wp, a.Ms, a.interp, f0.rc.su, ou, fu);
+            table_coord<R, EXT>(Wp, a.Ms, a.interp, f0.rc.sv, ov, fv);
+            stage_grid<W, R, EXT>(tab, Wp, a.interp, ou, fu, ov, fv, rec_row(f0.rc.rx) - row0, xrel,
+                                  f0.v.x * f0.wt, f0.v.y * f0.wt, s_cv, s_a, lane);
+          }
+          const unsigned cover = mine ? cover_lanes<W, KC>(xrel) : 0u;
           __syncwarp();
           unsigned M = transpose32(cover, lane);
-          if constexpr (!COMP) {
-            while (M) {
-              const int l1 = __ffs(M) - 1;
-              M &= M - 1u;
-              const bool two = M != 0u;
-              const int l2 = two ? __ffs(M) - 1 : l1;
-              if (two) M &= M - 1u;
-              const C2 a1 = s_a[l1 * W + (lane - s_x0[l1])];
-              C2 a2 = s_a[l2 * W + (lane - s_x0[l2])];
-              if (!two) { a2.x = R(0); a2.y = R(0); }
-#pragma unroll
-              for (int q = 0; q < TT; ++q) {
-                const R c1 = s_cv[q * Coop<W>::pitch + l1];
-                const R c2 = s_cv[q * Coop<W>::pitch + l2];
-                const int k = (gp * kD + q) % RS;
-                acc_re[k] = fma(c1, a1.x, fma(c2, a2.x, acc_re[k]));
-                acc_im[k] = fma(c1, a1.y, fma(c2, a2.y, acc_im[k]));
-              }
-            }
-          }
           while (M) {
-            const int l = __ffs(M) - 1;
+            const int l1 = __ffs(M) - 1;
             M &= M - 1u;
-            const C2 ai = s_a[l * W + (lane - s_x0[l])];
+            const bool two = M != 0u;
+            const int l2 = two ? __ffs(M) - 1 : l1;
+            if (two) M &= M - 1u;
+            P c1[NPR], c2[NPR];
+            load_cv_pairs<W, R>(s_cv, l1, c1);
+            load_cv_pairs<W, R>(s_cv, l2, c2);
+            R a1r[KC], a1i[KC], a2r[KC], a2i[KC];
+            load_cols<R, KC>(reinterpret_cast<const C2*>(s_a + (l1 * (L::PS + 1) + myslot) * L::SA), a1r, a1i);
+            load_cols<R, KC>(reinterpret_cast<const C2*>(s_a + (l2 * (L::PS + 1) + myslot) * L::SA), a2r, a2i);
+            if (!two) {
 #pragma unroll
-            for (int q = 0; q < TT; ++q) {
-              const R c = s_cv[q * Coop<W>::pitch + l];
-              const int k = (gp * kD + q) % RS;
-              if constexpr (COMP) {
-                two_sum_acc(acc_re[k], lo_re[k], c * ai.x);
-                two_sum_acc(acc_im[k], lo_im[k], c * ai.y);
-              } else {
-                acc_re[k] = fma(c, ai.x, acc_re[k]);
-                acc_im[k] = fma(c, ai.y, acc_im[k]);
+              for (int j = 0; j < KC; ++j) a2r[j] = a2i[j] = R(0);
+            }
+#pragma unroll
+            for (int j = 0; j < KC; ++j) {
+              const P d1r = pdup(a1r[j]), d1i = pdup(a1i[j]), d2r = pdup(a2r[j]), d2i = pdup(a2i[j]);
+#pragma unroll
+              for (int m = 0; m < NPR; ++m) {
+                const int h = (gp + m) % RH;
+                if constexpr (COMP) {
+                  two_sum_pair(accR[j][h], loR[j][h], pmul(c1[m], d1r));
+                  two_sum_pair(accI[j][h], loI[j][h], pmul(c1[m], d1i));
+                  two_sum_pair(accR[j][h], loR[j][h], pmul(c2[m], d2r));
+                  two_sum_pair(accI[j][h], loI[j][h], pmul(c2[m], d2i));
+                } else {
+                  accR[j][h] = pfma(c2[m], d2r, pfma(c1[m], d1r, accR[j][h]));
+                  accI[j][h] = pfma(c2[m], d2i, pfma(c1[m], d1i, accI[j][h]));
+                }
               }
             }
           }
@@ -414,65 +576,87 @@ __device__ __forceinline__ void grid_item(const SweepArgs& a, const R* __restric
             fetch_rec(wbase + 64, rend, f2);
           }
         }
-        // rows row0 .. row0 + kD - 1 are complete: store them and recycle their slots
+        // rows row0 and row0 + 1 (ring pair gp mod RH) are complete: store them, recycle
+        const int h = gp % RH;
 #pragma unroll
         for (int d = 0; d < kD; ++d) {
-          const int k = (gp * kD + d) % RS;
           if (gb + d < nrows) {
-            C2 o;
-            if constexpr (COMP) {
-              o.x = acc_re[k] + lo_re[k];
-              o.y = acc_im[k] + lo_im[k];
-            } else {
-              o.x = acc_re[k];
-              o.y = acc_im[k];
+            R orr[KC], oi[KC];
+#pragma unroll
+            for (int j = 0; j < KC; ++j) {
+              if constexpr (COMP) {
+                orr[j] = (d ? phi(accR[j][h]) : plo(accR[j][h])) + (d ? phi(loR[j][h]) : plo(loR[j][h]));
+                oi[j] = (d ? phi(accI[j][h]) : plo(accI[j][h])) + (d ? phi(loI[j][h]) : plo(loI[j][h]));
+              } else {
+                orr[j] = d ? phi(accR[j][h]) : plo(accR[j][h]);
+                oi[j] = d ? phi(accI[j][h]) : plo(accI[j][h]);
+              }
             }
-            grid[static_cast<size_t>(row0 + d) * N + col] = o;
-            acc_re[k] = acc_im[k] = lo_re[k] = lo_im[k] = R(0);
+            store_cols<R, KC>(grid + static_cast<size_t>(row0 + d) * N + col0, orr, oi);
           }
+        }
+#pragma unroll
+        for (int j = 0; j < KC; ++j) {
+          accR[j][h] = accI[j][h] = pzero<P>();
+          if constexpr (COMP) loR[j][h] = loI[j][h] = pzero<P>();
         }
       }
     }
   }
-  // spill: slot q holds relative row nrows + ((q - nrows) mod RS); the W - 1 rows after
-  // the item carry partial sums
-  C2* sp = spill + static_cast<size_t>(slot) * RS * kStrip;
+  // spill: ring pair h holds relative rows nrows + ((2h - nrows) mod RS) (and the next);
+  // the W - 1 rows after the item carry partial sums
+  C2* sp = spill + static_cast<size_t>(slot) * RS * S + KC * lane;
 #pragma unroll
-  for (int q = 0; q < RS; ++q) {
-    C2 o;
-    if constexpr (COMP) {
-      o.x = acc_re[q] + lo_re[q];
-      o.y = acc_im[q] + lo_im[q];
-    } else {
-      o.x = acc_re[q];
-      o.y = acc_im[q];
+  for (int h = 0; h < RH; ++h) {
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      R orr[KC], oi[KC];
+#pragma unroll
+      for (int j = 0; j < KC; ++j) {
+        if constexpr (COMP) {
+          orr[j] = (d ? phi(accR[j][h]) : plo(accR[j][h])) + (d ? phi(loR[j][h]) : plo(loR[j][h]));
+          oi[j] = (d ? phi(accI[j][h]) : plo(accI[j][h])) + (d ? phi(loI[j][h]) : plo(loI[j][h]));
+        } else {
+          orr[j] = d ? phi(accR[j][h]) : plo(accR[j][h]);
+          oi[j] = d ? phi(accI[j][h]) : plo(accI[j][h]);
+        }
+      }
+      store_cols<R, KC>(sp + static_cast<size_t>(2 * h + d) * S, orr, oi);
     }
-    sp[q * kStrip + lane] = o;
   }
 }
 
 // Spill rows of work item w, run by the 32 lanes of a warp after every item stored its own
 // rows: the W - 1 rows past the item (relative rows nrows + j, j < W - 1, held in ring slot
 // (nrows + j) mod RS) are added into the grid. All of them are loaded before the first
-// add, so that the warp waits for one round of loads.
+// add, so that the warp waits for one round of loads. S = 32 KC columns, KC per lane.
 template <typename R>
 __device__ __forceinline__ void spill_item(const Item* __restrict__ items, int nfront, int item_cap, int W, int RS,
-                                           int N, const typename Cplx<R>::T* __restrict__ spill,
+                                           int N, int S, const typename Cplx<R>::T* __restrict__ spill,
                                            typename Cplx<R>::T* __restrict__ grid, int w, int lane) {
   constexpr int kMaxRows = 15;  // W - 1 for W <= 16
+  constexpr int KC = cols_per_lane<R>();
   const int slot = item_slot(w, nfront, item_cap);
   const Item item = items[slot];
   const int nrows = item.r1 - item.r0;
   if (nrows <= 0 || item.nrec == 0) return;
-  const typename Cplx<R>::T* sp = spill + static_cast<size_t>(slot) * RS * kStrip + lane;
-  typename Cplx<R>::T v[kMaxRows];
+  const typename Cplx<R>::T* sp = spill + static_cast<size_t>(slot) * RS * S + KC * lane;
+  R vr[kMaxRows][KC], vi[kMaxRows][KC];
 #pragma unroll
   for (int j = 0; j < kMaxRows; ++j)
-    if (j < W - 1) v[j] = sp[((nrows + j) % RS) * kStrip];
-  typename Cplx<R>::T* g = grid + item.strip * kStrip + lane;
+    if (j < W - 1) load_cols<R, KC>(sp + static_cast<size_t>((nrows + j) % RS) * S, vr[j], vi[j]);
+  typename Cplx<R>::T* g = grid + static_cast<size_t>(item.strip) * S + KC * lane;
 #pragma unroll
   for (int j = 0; j < kMaxRows; ++j)
-    if (j < W - 1) red_add(g + static_cast<size_t>((item.r1 + j) % N) * N, v[j]);
+    if (j < W - 1) {
+#pragma unroll
+      for (int c = 0; c < KC; ++c) {
+        typename Cplx<R>::T v;
+        v.x = vr[j][c];
+        v.y = vi[j][c];
+        red_add(g + static_cast<size_t>((item.r1 + j) % N) * N + c, v);
+      }
+    }
 }
 
 // One degridding work item, run by the 32 lanes of a warp (see grid_item).
@@ -480,35 +664,44 @@ template <int W, typename R, bool EXT = false>
 __device__ __forceinline__ void degrid_item(const SweepArgs& a, const R* __restrict__ tab, unsigned char* my,
                                             const Item& item, int lane) {
   using C2 = typename Cplx<R>::T;
-  using St = Stage<W, R>;
-  constexpr int Wp = wpad<R>(W);
-  constexpr int RS = Ring<W>::R, P = Ring<W>::P, TT = Ring<W>::T;
-  constexpr bool kPk = sizeof(R) == 4;
-  int* s_x0 = reinterpret_cast<int*>(my);
-  R* s_cv = reinterpret_cast<R*>(my + St::x0_bytes);
-  R* s_cu = reinterpret_cast<R*>(my + St::x0_bytes + St::cv_bytes);
-  C2* s_p = reinterpret_cast<C2*>(my + St::x0_bytes + St::cv_bytes + St::cu_bytes);
+  using P = typename PairOf<R>::T;
+  using L = Lay<W, R>;
+  constexpr int KC = L::KC, S = 32 * KC;
+  constexpr int RS = Ring<W>::R, NP = Ring<W>::P, NPR = Ring<W>::TP / 2, RH = RS / 2;
+  unsigned char* s_cv = my;
+  unsigned char* s_u = my + L::cv_bytes;
+  unsigned char* s_p = my + L::cv_bytes + align16(L::u_bytes);
 
   const Rec* __restrict__ recs = a.recs;
   const C2* __restrict__ G = static_cast<const C2*>(a.grid_in);
   C2* __restrict__ out = static_cast<C2*>(a.vis_out);
-  const int N = a.N;
+  const int N = a.N, Wp = a.Wp;
 
   if (item.nrec == 0) return;
   const int* __restrict__ off = a.offsets + static_cast<long long>(item.strip) * N;
-  const int col = item.strip * kStrip + lane;
+  const int col0 = item.strip * S + KC * lane;
   const int nrows = item.r1 - item.r0;
-  // ring slot x % RS holds grid row item.r0 + x of column `col`; rows 0 .. TT - kD - 1
-  // are loaded up front, each group loads the kD rows that complete its window
-  R g_re[RS], g_im[RS];
-  unsigned long long g2[RS];
+  // ring pair h holds grid rows item.r0 + 2h' and + 1 (h' = h mod RH) of the lane's columns;
+  // rows 0 .. TP - 3 are loaded up front, each group loads the pair that completes its window
+  P gR[KC][RH], gI[KC][RH];
+  auto load_pair = [&](int x, int h) {  // relative rows x, x + 1 into ring pair h
+    R r0[KC], i0[KC], r1[KC], i1[KC];
+    load_cols<R, KC>(G + static_cast<size_t>((item.r0 + x) % N) * N + col0, r0, i0);
+    load_cols<R, KC>(G + static_cast<size_t>((item.r0 + x + 1) % N) * N + col0, r1, i1);
 #pragma unroll
-  for (int x = 0; x < TT - kD; ++x) {
-    const C2 v = G[static_cast<size_t>((item.r0 + x) % N) * N + col];
-    g_re[x] = v.x;
-    g_im[x] = v.y;
-    if constexpr (kPk) g2[x] = f2pack(float(v.x), float(v.y));
-  }
+    for (int j = 0; j < KC; ++j) {
+      if constexpr (sizeof(R) == 4) {
+        gR[j][h] = f2pack(r0[j], r1[j]);
+        gI[j][h] = f2pack(i0[j], i1[j]);
+      } else {
+        gR[j][h] = make_double2(r0[j], r1[j]);
+        gI[j][h] = make_double2(i0[j], i1[j]);
+      }
+    }
+  };
+#pragma unroll
+  for (int h = 0; h < NPR - 1; ++h) load_pair(2 * h, h);
+  const int myslot = lane & (L::PS - 1);
   const int rb = off[item.r0], rend = off[item.r1];
   int wbase = rb, cstart = rb;
   Rec rc0{0u, 0, 0u, 0u}, rc1{0u, 0, 0u, 0u}, rc2{0u, 0, 0u, 0u};
@@ -517,93 +710,89 @@ __device__ __forceinline__ void degrid_item(const SweepArgs& a, const R* __restr
   if (rb + 64 + lane < rend) rc2 = recs[rb + 64 + lane];
   for (int g0 = 0; g0 < nrows; g0 += RS) {
 #pragma unroll
-    for (int gp = 0; gp < P; ++gp) {
+    for (int gp = 0; gp < NP; ++gp) {
       const int gb = g0 + gp * kD;
       if (gb < nrows) {
         const int row0 = item.r0 + gb;
-#pragma unroll
-        for (int d = 0; d < kD; ++d) {
-          const int x = gb + TT - kD + d;
-          const C2 v = G[static_cast<size_t>((item.r0 + x) % N) * N + col];
-          g_re[(gp * kD + TT - kD + d) % RS] = v.x;
-          g_im[(gp * kD + TT - kD + d) % RS] = v.y;
-          if constexpr (kPk) g2[(gp * kD + TT - kD + d) % RS] = f2pack(float(v.x), float(v.y));
-        }
+        load_pair(gb + 2 * (NPR - 1), (gp + NPR - 1) % RH);
         const int re = off[min(row0 + kD, item.r1)];
         while (cstart < re) {
           const int ce = min(re, wbase + 32);
-          const int lo = cstart - wbase, hi = ce - wbase;
-          const bool mine = lane >= lo && lane < hi;
+          const bool mine = lane >= cstart - wbase && lane < ce - wbase;
           const int xrel = rec_xrel(rc0.rx);
-          if (mine) s_x0[lane] = xrel;
-          int ou, ov;
-          R fu, fv;
-          table_coord<R, EXT>(Wp, a.Ms, a.interp, rc0.su, ou, fu);
-          table_coord<R, EXT>(Wp, a.Ms, a.interp, rc0.sv, ov, fv);
-          stage_chunk<W, R, false, EXT>(tab, Wp, a.interp, lo, hi, ou, fu, ov, fv, rec_row(rc0.rx) - row0, R(0), R(0),
-                                   s_cv, s_cu, lane);
-          const unsigned cover = mine ? cover_mask(xrel, W) : 0u;
+          if (mine) {
+            int ou, ov;
+            R fu, fv;
+            table_coord<R, EXT>(Wp, a.Ms, a.interp, rc0.su, ou, fu);
+            table_coord<R, EXT>(Wp, a.Ms, a.interp, rc0.sv, ov, fv);
+            stage_degrid<W, R, EXT>(tab, Wp, a.interp, ou, fu, ov, fv, rec_row(rc0.rx) - row0, xrel, s_cv, s_u,
+                                    lane);
+          }
+          const unsigned cover = mine ? cover_lanes<W, KC>(xrel) : 0u;
           __syncwarp();
           unsigned M = transpose32(cover, lane);
-          if constexpr (kPk) {
-            while (M) {
-              const int l1 = __ffs(M) - 1;
-              M &= M - 1u;
-              const bool two = M != 0u;
-              const int l2 = two ? __ffs(M) - 1 : l1;
-              if (two) M &= M - 1u;
-              const int i1 = lane - s_x0[l1], i2 = lane - s_x0[l2];
-              unsigned long long s1 = 0ull, s2 = 0ull;
-#pragma unroll
-              for (int q = 0; q < TT; ++q) {
-                const R c1 = s_cv[q * Coop<W>::pitch + l1];
-                const R c2 = s_cv[q * Coop<W>::pitch + l2];
-                s1 = f2fma(f2pack(c1, c1), g2[(gp * kD + q) % RS], s1);
-                s2 = f2fma(f2pack(c2, c2), g2[(gp * kD + q) % RS], s2);
-              }
-              s_p[l1 * W + i1] = f2unpack(s1);
-              if (two) s_p[l2 * W + i2] = f2unpack(s2);
-            }
-          }
           while (M) {
-            const int l = __ffs(M) - 1;
+            const int l1 = __ffs(M) - 1;
             M &= M - 1u;
-            const int i = lane - s_x0[l];
-            R sr = R(0), si = R(0);
-            if constexpr (kPk) {
-              unsigned long long s2 = 0ull;
-#pragma unroll
-              for (int q = 0; q < TT; ++q) {
-                const R c = s_cv[q * Coop<W>::pitch + l];
-                s2 = f2fma(f2pack(c, c), g2[(gp * kD + q) % RS], s2);
-              }
-              const float2 f = f2unpack(s2);
-              sr = f.x;
-              si = f.y;
-            } else {
-#pragma unroll
-              for (int q = 0; q < TT; ++q) {
-                const R c = s_cv[q * Coop<W>::pitch + l];
-                sr = fma(c, g_re[(gp * kD + q) % RS], sr);
-                si = fma(c, g_im[(gp * kD + q) % RS], si);
+            const bool two = M != 0u;
+            const int l2 = two ? __ffs(M) - 1 : l1;
+            if (two) M &= M - 1u;
+            P c1[NPR], c2[NPR];
+            load_cv_pairs<W, R>(s_cv, l1, c1);
+            load_cv_pairs<W, R>(s_cv, l2, c2);
+            R u1[KC], u2[KC];
+            {
+              const unsigned char* p1 = s_u + (l1 * (L::PS + 1) + myslot) * L::SU;
+              const unsigned char* p2 = s_u + (l2 * (L::PS + 1) + myslot) * L::SU;
+              if constexpr (sizeof(R) == 4 && KC == 2) {
+                const float2 x1 = *reinterpret_cast<const float2*>(p1), x2 = *reinterpret_cast<const float2*>(p2);
+                u1[0] = x1.x;
+                u1[1] = x1.y;
+                u2[0] = x2.x;
+                u2[1] = x2.y;
+              } else {
+                u1[0] = *reinterpret_cast<const R*>(p1);
+                u2[0] = *reinterpret_cast<const R*>(p2);
               }
             }
-            C2 p;
-            p.x = sr;
-            p.y = si;
-            s_p[l * W + i] = p;
+            R p1r = R(0), p1i = R(0), p2r = R(0), p2i = R(0);
+#pragma unroll
+            for (int j = 0; j < KC; ++j) {
+              P s1r = pzero<P>(), s1i = pzero<P>(), s2r = pzero<P>(), s2i = pzero<P>();
+#pragma unroll
+              for (int m = 0; m < NPR; ++m) {
+                const int h = (gp + m) % RH;
+                s1r = pfma(c1[m], gR[j][h], s1r);
+                s1i = pfma(c1[m], gI[j][h], s1i);
+                s2r = pfma(c2[m], gR[j][h], s2r);
+                s2i = pfma(c2[m], gI[j][h], s2i);
+              }
+              p1r = fma(u1[j], psum(s1r), p1r);
+              p1i = fma(u1[j], psum(s1i), p1i);
+              p2r = fma(u2[j], psum(s2r), p2r);
+              p2i = fma(u2[j], psum(s2i), p2i);
+            }
+            C2 o1, o2;
+            o1.x = p1r;
+            o1.y = p1i;
+            o2.x = p2r;
+            o2.y = p2i;
+            *reinterpret_cast<C2*>(s_p + (l1 * (L::PS + 1) + myslot) * L::SP) = o1;
+            if (two) *reinterpret_cast<C2*>(s_p + (l2 * (L::PS + 1) + myslot) * L::SP) = o2;
           }
           __syncwarp();
           if (mine) {
-            const int i0 = max(0, -xrel), i1 = min(W, kStrip - xrel);
+            // the record's lane adds the partial sums of the lanes its support covers
+            const int L0 = xrel >> (KC - 1), L1 = (xrel + W - 1) >> (KC - 1);
             R vr = R(0), vi = R(0);
 #pragma unroll
-            for (int ii = 0; ii < W; ++ii) {
-              if (ii < i0 || ii >= i1) continue;
-              const C2 p = s_p[lane * W + ii];
-              const R c = s_cu[lane * W + ii];
-              vr = fma(c, p.x, vr);
-              vi = fma(c, p.y, vi);
+            for (int m = 0; m < L::NL; ++m) {
+              const int Ln = L0 + m;
+              if (Ln >= 0 && Ln <= 31 && Ln <= L1) {
+                const C2 p = *reinterpret_cast<const C2*>(s_p + (lane * (L::PS + 1) + (Ln & (L::PS - 1))) * L::SP);
+                vr += p.x;
+                vi += p.y;
+              }
             }
             C2 o;
             o.x = vr;
@@ -635,7 +824,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks<W, R, COMP, EXT>()) k_gri
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const R* tab = stage_table<R>(a.table, (a.Ms + 1) * a.Wp, a.table_in_smem != 0, smem);
   const size_t tab_bytes = a.table_in_smem ? align16(size_t(a.Ms + 1) * a.Wp * sizeof(R)) : 0;
-  unsigned char* my = smem + tab_bytes + warp * align16(Stage<W, R>::grid_bytes);
+  unsigned char* my = smem + tab_bytes + warp * Lay<W, R>::grid_bytes;
   int nfront;
   const int total = work_total(a.counters, a.item_cap, nfront);
   for (int w = next_item(a.counters + kCntGridWork, lane); w < total; w = next_item(a.counters + kCntGridWork, lane))
@@ -648,7 +837,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks<W, R, false, EXT>()) k_de
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const R* tab = stage_table<R>(a.table, (a.Ms + 1) * a.Wp, a.table_in_smem != 0, smem);
   const size_t tab_bytes = a.table_in_smem ? align16(size_t(a.Ms + 1) * a.Wp * sizeof(R)) : 0;
-  unsigned char* my = smem + tab_bytes + warp * align16(Stage<W, R>::degrid_bytes);
+  unsigned char* my = smem + tab_bytes + warp * Lay<W, R>::degrid_bytes;
   int nfront;
   const int total = work_total(a.counters, a.item_cap, nfront);
   for (int w = next_item(a.counters + kCntDegridWork, lane); w < total;
@@ -690,12 +879,30 @@ template <bool EXT> void* sweep_kernel_pick(int W, int dtype, int accum, bool de
 }
 
 // Staging bytes of one warp (runtime W).
+template <int W> size_t stage_bytes_w(int dtype, bool degrid) {
+  if (dtype) return degrid ? Lay<W, double>::degrid_bytes : Lay<W, double>::grid_bytes;
+  return degrid ? Lay<W, float>::degrid_bytes : Lay<W, float>::grid_bytes;
+}
 inline size_t stage_bytes(int W, int dtype, bool degrid) {
-  const size_t rs = dtype ? 8 : 4;
-  const int T = W + kD - 1;
-  const size_t x0 = 32 * sizeof(int), cv = align16(size_t(T) * (32 + 32 / coop_group(W)) * rs),
-               cu = 32 * size_t(W) * rs, ab = 32 * W * 2 * rs;
-  return align16(x0 + cv + (degrid ? cu : 0) + ab);
+  switch (W) {
+    case 1: return stage_bytes_w<1>(dtype, degrid);
+    case 2: return stage_bytes_w<2>(dtype, degrid);
+    case 3: return stage_bytes_w<3>(dtype, degrid);
+    case 4: return stage_bytes_w<4>(dtype, degrid);
+    case 5: return stage_bytes_w<5>(dtype, degrid);
+    case 6: return stage_bytes_w<6>(dtype, degrid);
+    case 7: return stage_bytes_w<7>(dtype, degrid);
+    case 8: return stage_bytes_w<8>(dtype, degrid);
+    case 9: return stage_bytes_w<9>(dtype, degrid);
+    case 10: return stage_bytes_w<10>(dtype, degrid);
+    case 11: return stage_bytes_w<11>(dtype, degrid);
+    case 12: return stage_bytes_w<12>(dtype, degrid);
+    case 13: return stage_bytes_w<13>(dtype, degrid);
+    case 14: return stage_bytes_w<14>(dtype, degrid);
+    case 15: return stage_bytes_w<15>(dtype, degrid);
+    case 16: return stage_bytes_w<16>(dtype, degrid);
+    default: return 0;
+  }
 }
 
 }  // namespace

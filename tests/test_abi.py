@@ -140,7 +140,7 @@ def test_plan_argument_errors_precede_device_work(lmg):
     L = lmg.lib()
     for n_img, scale, maxv, dtype, msg in ((63, 1e-3, 10, 0, "n_image"), (64, 0.0, 10, 0, "pixel_scale"),
                                            (64, 1e-3, 0, 0, "max_vis"), (64, 1e-3, 10, 3, "dtype"),
-                                           (40, 1e-3, 10, 0, "multiple of 32")):
+                                           (40, 1e-3, 10, 0, "multiple of 64"), (48, 1e-3, 10, 0, "multiple of 64")):
         assert L.lmg_plan_create(t._h, n_img, scale, maxv, dtype, ctypes.byref(h)) == -1
         assert msg in L.lmg_last_error().decode()
 
