@@ -60,25 +60,65 @@ def s_float32(S):
 
 
 def s_float64(S):
-    """Table coordinate in float64 (exact: S < 2^32)."""
+    """Table coordinate of the quantised position in float64 (exact: S < 2^32)."""
     return np.asarray(S, dtype=np.float64) * 2.0 ** -FRAC_BITS
+
+
+def s_exact(u_cells, S):
+    """Table coordinate of the unquantised position, s = n_start - (u - W/2), as
+    fl(S 2^-32 + delta) with delta = u_q - u = (U - u 2^32) 2^-32 (exact: U is the
+    integer nearest to u 2^32), so that the fraction keeps the full float64 precision of
+    u while n_start comes from the exact integer rule. Invalid positions give 0."""
+    u = np.asarray(u_cells, dtype=np.float64)
+    valid = np.isfinite(u) & (np.abs(u) < MAX_ABS_CELLS)
+    p = np.ldexp(np.where(valid, u, 0.0), FRAC_BITS)
+    U = np.rint(p)
+    delta = np.ldexp(U - p, -FRAC_BITS)
+    return np.where(valid, s_float64(S) + delta, 0.0)
+
+
+def table_lookup(T, Ms, S, s, interp):
+    """Table weights (Section 5.1, Appendix F) with the row decision taken on the fixed-point
+    coordinate S (exact integers: nearest row (S Ms + 2^31) >> 32, linear row (S Ms) >> 32,
+    Lagrange first row ((S Ms) - (d - 1) 2^31) >> 32 clamped to [0, Ms - d]), identical on
+    every implementation, and the interpolation fraction from the float64 coordinate s:
+    t = s Ms, f = t - k."""
+    P = np.asarray(S, dtype=np.int64) * np.int64(Ms)        # < 2^52
+    t = np.asarray(s, dtype=np.float64) * Ms
+    if interp == D.INTERP_NEAREST:
+        return T[(P + (1 << (FRAC_BITS - 1))) >> FRAC_BITS]
+    if interp == D.INTERP_LINEAR:
+        k = P >> FRAC_BITS
+        f = (t - k)[:, None]
+        return (1.0 - f) * T[k] + f * T[k + 1]
+    d = interp
+    k0 = np.clip((P - (d - 1) * (1 << (FRAC_BITS - 1))) >> FRAC_BITS, 0, Ms - d)
+    L = D.lagrange_basis(t - k0, d)
+    return sum(L[:, m, None] * T[k0 + m] for m in range(d + 1))
 
 
 class Plan:
     """Support starts and table coordinates for a set of (u, v) cell positions.
 
-    The coordinates are exact float64 values of s (the default, used by every parity
-    reference). ``single_precision_s=True`` is a named diagnostic that rounds s to float32
-    and takes the nearest-row decision in float32."""
+    The support starts and table rows come from the exact integer rule on the positions
+    quantised to 2^-32 cell; the table coordinate s itself keeps the full float64 precision
+    of the position (``s_exact``; the default, used by every parity reference). Two named
+    diagnostics replace it: ``quantized_s=True`` uses the quantised coordinate S 2^-32 (its
+    position error of up to 2^-33 cell bounds float64 results near 1e-10), and
+    ``single_precision_s=True`` rounds that to float32 and takes the nearest-row decision in
+    float32."""
 
-    def __init__(self, u_cells, v_cells, W, N, single_precision_s=False):
+    def __init__(self, u_cells, v_cells, W, N, single_precision_s=False, quantized_s=False):
         self.W, self.N = W, N
-        self.n0, Su, vu = support_rule(u_cells, W)
-        self.m0, Sv, vv = support_rule(v_cells, W)
+        self.n0, self.Su, vu = support_rule(u_cells, W)
+        self.m0, self.Sv, vv = support_rule(v_cells, W)
         self.valid = vu & vv
-        conv = s_float32 if single_precision_s else s_float64
-        self.su = conv(Su).astype(np.float64)
-        self.sv = conv(Sv).astype(np.float64)
+        if single_precision_s:
+            self.su, self.sv = s_float32(self.Su).astype(np.float64), s_float32(self.Sv).astype(np.float64)
+        elif quantized_s:
+            self.su, self.sv = s_float64(self.Su), s_float64(self.Sv)
+        else:
+            self.su, self.sv = s_exact(u_cells, self.Su), s_exact(v_cells, self.Sv)
         self.single = single_precision_s
 
     def weights(self, T, Ms, interp):
@@ -86,10 +126,12 @@ class Plan:
         when T is a function of s (direct calculation, Section 5.2), T(s) itself."""
         if callable(T):
             Cu, Cv = T(self.su), T(self.sv)
+        elif self.single:
+            Cu = D.table_weights(T, Ms, self.su, interp, np.float32)
+            Cv = D.table_weights(T, Ms, self.sv, interp, np.float32)
         else:
-            dd = np.float32 if self.single else np.float64
-            Cu = D.table_weights(T, Ms, self.su, interp, dd)
-            Cv = D.table_weights(T, Ms, self.sv, interp, dd)
+            Cu = table_lookup(T, Ms, self.Su, self.su, interp)
+            Cv = table_lookup(T, Ms, self.Sv, self.sv, interp)
         Cu[~self.valid] = 0.0
         Cv[~self.valid] = 0.0
         return Cu, Cv

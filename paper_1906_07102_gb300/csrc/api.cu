@@ -86,7 +86,7 @@ namespace lmg {
 void free_plan(lmg_plan* p) {
   if (!p) return;
   void* ptrs[] = {p->d_table, p->d_h, p->hist, p->offsets, p->rank, p->partial, p->recs,
-                  p->items, p->counters, p->spill, p->work, p->model};
+                  p->items, p->counters, p->spill, p->frac, p->work, p->model};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->fft_ok) cufftDestroy(p->fft);
@@ -116,6 +116,7 @@ SweepArgs sweep_args(const lmg_plan* p) {
   a.dtype = p->dtype;
   a.item_cap = p->item_cap;
   a.nvis = p->nvis;
+  a.frac = p->frac;
   return a;
 }
 
@@ -312,6 +313,7 @@ int plan_create(const lmg_table* t, int64_t n_image, double pixel_scale, int64_t
       (rc = dalloc(&p->partial, size_t(p->nchunks), "scan")) || (rc = dalloc(&p->recs, size_t(2 * max_vis), "records")) ||
       (rc = dalloc(&p->items, size_t(p->item_cap), "items")) || (rc = dalloc(&p->counters, kNumCounters, "counters")) ||
       (rc = dalloc(reinterpret_cast<unsigned char**>(&p->spill), size_t(p->item_cap) * ring_slots(p->W) * strip * c2, "spill")) ||
+      (dtype == LMG_C128 && (rc = dalloc(&p->frac, size_t(max_vis), "quantisation residuals"))) ||
       (opt.work_grid && (rc = dalloc(reinterpret_cast<unsigned char**>(&p->work), size_t(N) * size_t(N) * c2, "work grid"))) ||
       (opt.work_grid && (rc = dalloc(reinterpret_cast<unsigned char**>(&p->model), size_t(N) * size_t(N) * c2, "model grid")))) {
     free_plan(p);
@@ -409,6 +411,7 @@ int plan_bin(lmg_plan* p, const double* uv, int64_t nvis, cudaStream_t st) {
   a.recs = p->recs;
   a.items = p->items;
   a.counters = p->counters;
+  a.frac = p->frac;
   const int rc = launch_status(bin_launch(a, st), "binning");
   if (rc == LMG_OK) p->nvis = nvis;
   return rc;

@@ -23,9 +23,11 @@ namespace {
 
 // Support start (grid indices, wrapped to [0, N)) and table coordinates of position p =
 // (u, v); false for a dropped position (product not finite or |u| N pixel_scale >= 2^30).
-__device__ __forceinline__ bool vis_position(double2 p, double scale2, int W, int N, VisPos& vp) {
+__device__ __forceinline__ bool vis_position(double2 p, double scale2, int W, int N, VisPos& vp,
+                                             double2* delta = nullptr) {
   long long U, V;
   if (!fixed_position(p.x, scale2, U) || !fixed_position(p.y, scale2, V)) return false;
+  if (delta) *delta = make_double2(quantisation_residual(p.x, scale2, U), quantisation_residual(p.y, scale2, V));
   long long n0, m0;
   support_start(U, W, n0, vp.su);
   support_start(V, W, m0, vp.sv);
@@ -46,7 +48,7 @@ constexpr int kCountIlp = 4;
 
 __global__ void k_bin_count(const double* __restrict__ uv, long long nvis, double scale2, int W,
                             int N, int n_strips, int strip_w, int2* __restrict__ rank, int* __restrict__ hist,
-                            int* __restrict__ counters) {
+                            int* __restrict__ counters, double2* __restrict__ frac) {
   const int lane = threadIdx.x & 31;  // for the dropped-position count
   const long long span = static_cast<long long>(blockDim.x) * kCountIlp;
   const long long stride = static_cast<long long>(gridDim.x) * span;
@@ -61,7 +63,11 @@ __global__ void k_bin_count(const double* __restrict__ uv, long long nvis, doubl
       bad[u] = false;
       vp[u] = VisPos{-1, 0, 0u, 0u};
       if (k < nvis) {
-        if (vis_position(reinterpret_cast<const double2*>(uv)[k], scale2, W, N, vp[u])) {
+        double2 dl = make_double2(0.0, 0.0);
+        const bool ok = vis_position(reinterpret_cast<const double2*>(uv)[k], scale2, W, N, vp[u],
+                                     frac != nullptr ? &dl : nullptr);
+        if (frac != nullptr) frac[k] = dl;
+        if (ok) {
           const int strip = vp[u].x0 / strip_w;
           key1[u] = strip * N + vp[u].y0;
           if ((vp[u].x0 % strip_w) + W > strip_w) key2[u] = ((strip + 1) % n_strips) * N + vp[u].y0;
@@ -298,7 +304,7 @@ int bin_launch(const BinArgs& a, cudaStream_t st) {
   const long long want_c = (a.nvis + threads * kCountIlp - 1) / (threads * kCountIlp);
   const int blocks_c = static_cast<int>(want_c < a.max_blocks ? (want_c > 0 ? want_c : 1) : a.max_blocks);
   k_bin_count<<<blocks_c, threads, 0, st>>>(a.uv, a.nvis, a.scale2, a.W, a.N, a.n_strips, a.strip, a.rank,
-                                          a.hist, a.counters);
+                                          a.hist, a.counters, a.frac);
   const int nchunks = static_cast<int>((L + kScanChunk - 1) / kScanChunk);
   k_scan_partials<<<nchunks, kScanThreads, 0, st>>>(a.hist, L, a.partial);
   k_scan_top<<<1, 1024, 0, st>>>(a.partial, nchunks);

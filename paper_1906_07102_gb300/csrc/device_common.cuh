@@ -70,6 +70,14 @@ __device__ __forceinline__ bool fixed_position(double u, double scale2, long lon
   return true;
 }
 
+// Residual u_q - u (cells) of the quantisation U = round(u scale2), scale2 = N pixel_scale
+// 2^32: (U - fl(u scale2)) 2^-32, exact (U and the product differ by at most 1/2, and U
+// converts to double exactly wherever the product has a fraction).
+__device__ __forceinline__ double quantisation_residual(double u, double scale2, long long U) {
+  const double p = __dmul_rn(u, scale2);
+  return __dmul_rn(__dsub_rn(static_cast<double>(U), p), 2.3283064365386962890625e-10);
+}
+
 // Support rule (Eq. 6): n_start = ceil(u - W/2) and S = (n_start - (u - W/2)) 2^32.
 __device__ __forceinline__ void support_start(long long U, int W, long long& n_start, unsigned& S) {
   const long long Y = U - (W & 1) * (1ll << (kFracBits - 1));

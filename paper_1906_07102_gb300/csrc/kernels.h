@@ -53,6 +53,8 @@ struct BinArgs {
   Rec* recs;       // 2 * max_vis
   Item* items;     // item_cap
   int* counters;   // 8
+  double2* frac;   // max_vis or NULL: per visibility (u_q - u, v_q - v) in cells, the residual
+                   // of the 2^-32 quantisation (float64 plans: exact table fractions)
 };
 
 int bin_launch(const BinArgs& a, cudaStream_t st);
@@ -82,6 +84,7 @@ struct SweepArgs {
   const void* grid_in;
   void* vis_out;
   long long nvis;
+  const double2* frac;  // float64 plans: quantisation residuals (BinArgs::frac), else NULL
 };
 
 int grid_launch(const SweepArgs& a, cudaStream_t st);

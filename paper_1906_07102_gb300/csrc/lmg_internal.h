@@ -80,6 +80,7 @@ struct lmg_plan {
   lmg::Item* items = nullptr;
   int* counters = nullptr;
   void* spill = nullptr;
+  double2* frac = nullptr;   // float64 plans: quantisation residual of every position
   void* work = nullptr;      // N x N work grid (null in batch channels)
   void* model = nullptr;     // N x N model grid of lmg_predict_vis: zero outside the kept rows
   cufftHandle fft = 0;              // full 2-D transform (lmg_fft)

@@ -69,15 +69,23 @@ template <int W, typename R> struct Lay {
   // lanes one record can cover, and the slots per record (a power of two >= NL)
   static constexpr int NL = (W - 1 + KC - 1) / KC + 1;
   static constexpr int PS = NL <= 2 ? 2 : (NL <= 4 ? 4 : (NL <= 8 ? 8 : 16));
-  // slot sizes: KC complex (gridding a = Cu w V), KC reals (degridding Cu), one complex
-  // (degridding partial sum); each record holds PS + 1 slots (odd pitch: spreads banks)
+  // slot sizes: the KC complex column weights a = Cu w V of gridding, KC reals Cu
+  // (degridding), one complex (degridding partial sum). A record's slots are followed by 16 bytes of padding,
+  // an odd number of 16-byte units per record (or of 8-byte words for 8-byte slots), which
+  // spreads the records over the banks.
   static constexpr int SA = KC * 2 * int(sizeof(R));
   static constexpr int SU = KC * int(sizeof(R));
   static constexpr int SP = 2 * int(sizeof(R));
-  static constexpr size_t cv_bytes = size_t(32) * CVS * sizeof(R);
-  static constexpr size_t a_bytes = size_t(32) * (PS + 1) * SA;
-  static constexpr size_t u_bytes = size_t(32) * (PS + 1) * SU;
-  static constexpr size_t p_bytes = size_t(32) * (PS + 1) * SP;
+  static constexpr int AP = PS * SA + 16;
+  static constexpr int UP = (PS + 1) * SU;
+  static constexpr int PP = (PS + 1) * SP;
+  // 33 records per chunk area: record 32 stays zero and stands in for a missing second
+  // record of an inner-loop iteration
+  static constexpr int NREC = 33;
+  static constexpr size_t cv_bytes = size_t(NREC) * CVS * sizeof(R);
+  static constexpr size_t a_bytes = size_t(NREC) * AP;
+  static constexpr size_t u_bytes = size_t(NREC) * UP;
+  static constexpr size_t p_bytes = size_t(NREC) * PP;
   static constexpr size_t grid_bytes = align16(cv_bytes + a_bytes);
   static constexpr size_t degrid_bytes = align16(cv_bytes + align16(u_bytes) + p_bytes);
 };
@@ -155,6 +163,53 @@ __device__ __forceinline__ void table_coord(int Wp, int Ms, int interp, unsigned
     off = static_cast<int>(k0) * Wp;
     f = static_cast<R>(P - (k0 << 32)) * static_cast<R>(2.3283064365386962890625e-10);
   }
+}
+
+// The same for float64 plans from the exact coordinate s = fl(S 2^-32 + delta), delta the
+// quantisation residual u_q - u of the binning: rows as above from the integer product
+// S Ms, fraction f = fl(s Ms) - k (and f = s for the direct calculation), so that the
+// weights keep the full float64 precision of the position.
+template <bool EXT>
+__device__ __forceinline__ void table_coord_exact(int Wp, int Ms, int interp, unsigned S, double delta, int& off,
+                                                  double& f) {
+  const double s = __dadd_rn(static_cast<double>(S) * 2.3283064365386962890625e-10, delta);
+  const double t = __dmul_rn(s, static_cast<double>(Ms));
+  const unsigned long long Pm = static_cast<unsigned long long>(S) * static_cast<unsigned>(Ms);
+  if constexpr (!EXT) {
+    if (interp) {
+      const long long k = static_cast<long long>(Pm >> 32);
+      off = static_cast<int>(k) * Wp;
+      f = __dsub_rn(t, static_cast<double>(k));
+    } else {
+      off = static_cast<int>((Pm + 0x80000000ull) >> 32) * Wp;
+      f = 0.0;
+    }
+  } else if (interp == 4) {
+    off = 0;
+    f = s;
+  } else {
+    const long long P = static_cast<long long>(Pm);
+    long long k0 = (P - static_cast<long long>(interp - 1) * 0x80000000ll) >> 32;
+    k0 = k0 < 0 ? 0 : (k0 > Ms - interp ? Ms - interp : k0);
+    off = static_cast<int>(k0) * Wp;
+    f = __dsub_rn(t, static_cast<double>(k0));
+  }
+}
+
+// Row offsets and fractions of a record for both axes (exact coordinates for float64 plans
+// that carry quantisation residuals).
+template <typename R, bool EXT>
+__device__ __forceinline__ void record_coords(const SweepArgs& a, const Rec& rc, int& ou, R& fu, int& ov, R& fv) {
+  if constexpr (sizeof(R) == 8) {
+    if (a.frac != nullptr) {
+      const double2 dl = a.frac[rc.idx];
+      table_coord_exact<EXT>(a.Wp, a.Ms, a.interp, rc.su, dl.x, ou, fu);
+      table_coord_exact<EXT>(a.Wp, a.Ms, a.interp, rc.sv, dl.y, ov, fv);
+      return;
+    }
+  }
+  table_coord<R, EXT>(a.Wp, a.Ms, a.interp, rc.su, ou, fu);
+  table_coord<R, EXT>(a.Wp, a.Ms, a.interp, rc.sv, ov, fv);
 }
 
 // Direct calculation (Section 5.2, float64 plans): C_a(s) = sum_k alpha[a][k] cos(k phi s) +
@@ -282,7 +337,7 @@ __device__ __forceinline__ void stage_grid(const R* __restrict__ tab, int Wp, in
   lookup<W, R, EXT>(tab, Wp, interp, ou, fu, cu);
   lookup<W, R, EXT>(tab, Wp, interp, ov, fv, cv);
   stage_cv<W, R>(cv, d, reinterpret_cast<R*>(s_cv) + lane * L::CVS);
-  unsigned char* rec = s_a + lane * (L::PS + 1) * L::SA;
+  unsigned char* rec = s_a + lane * L::AP;
   const int L0 = xrel >> (KC - 1), par = xrel & (KC - 1);
 #pragma unroll
   for (int m = 0; m < L::NL; ++m) {
@@ -302,10 +357,9 @@ __device__ __forceinline__ void stage_grid(const R* __restrict__ tab, int Wp, in
       v[2 * j + 1] = im;
     }
     unsigned char* dst = rec + ((L0 + m) & (L::PS - 1)) * L::SA;
-    if constexpr (sizeof(R) == 4 && KC == 2) {
+    if constexpr (sizeof(R) == 4) {
+      static_assert(KC == 2, "complex64 lanes own two columns");
       *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
-    } else if constexpr (sizeof(R) == 4) {
-      *reinterpret_cast<float2*>(dst) = make_float2(v[0], v[1]);
     } else {
 #pragma unroll
       for (int j = 0; j < KC; ++j) reinterpret_cast<double2*>(dst)[j] = make_double2(v[2 * j], v[2 * j + 1]);
@@ -324,7 +378,7 @@ __device__ __forceinline__ void stage_degrid(const R* __restrict__ tab, int Wp, 
   lookup<W, R, EXT>(tab, Wp, interp, ou, fu, cu);
   lookup<W, R, EXT>(tab, Wp, interp, ov, fv, cv);
   stage_cv<W, R>(cv, d, reinterpret_cast<R*>(s_cv) + lane * L::CVS);
-  unsigned char* rec = s_u + lane * (L::PS + 1) * L::SU;
+  unsigned char* rec = s_u + lane * L::UP;
   const int L0 = xrel >> (KC - 1), par = xrel & (KC - 1);
 #pragma unroll
   for (int m = 0; m < L::NL; ++m) {
@@ -343,6 +397,17 @@ __device__ __forceinline__ void stage_degrid(const R* __restrict__ tab, int Wp, 
     if constexpr (sizeof(R) == 4 && KC == 2) *reinterpret_cast<float2*>(dst) = make_float2(v[0], v[1]);
     else *reinterpret_cast<R*>(dst) = v[0];
   }
+}
+
+// Zeroes the stand-in record 32 of a warp's staging area (its Cv' and its slots).
+__device__ __forceinline__ void zero_bytes(unsigned char* p, int bytes, int lane) {
+  for (int i = 4 * lane; i < bytes; i += 128) *reinterpret_cast<int*>(p + i) = 0;
+}
+
+// Support-start row offsets of an item's row pairs, 32 pairs per block: lane t holds the
+// end offset of pair 32 b + t (the offset of row min(r0 + 2 (32 b + t + 1), r1)).
+__device__ __forceinline__ int pair_ends(const int* __restrict__ off, const Item& item, int b, int lane) {
+  return off[min(item.r0 + 2 * (32 * b + lane + 1), item.r1)];
 }
 
 // Lanes L0 .. L1 (inclusive) intersected with [0, 32).
@@ -426,6 +491,28 @@ __device__ __forceinline__ void load_cols(const typename Cplx<R>::T* src, R (&re
   }
 }
 
+// Loads one gridding slot (KC complex a = Cu w V) as (a_re, a_re) and (a_im, a_im) per column,
+// ready for the packed FMA (measured faster than staging the pairs duplicated, which doubles
+// the slot loads).
+template <typename R, int KC>
+__device__ __forceinline__ void load_slot(const unsigned char* p, typename PairOf<R>::T (&a)[KC][2]) {
+  if constexpr (sizeof(R) == 4) {
+    static_assert(KC == 2, "complex64 lanes own two columns");
+    const float4 x = *reinterpret_cast<const float4*>(p);
+    a[0][0] = pdup(x.x);
+    a[0][1] = pdup(x.y);
+    a[1][0] = pdup(x.z);
+    a[1][1] = pdup(x.w);
+  } else {
+#pragma unroll
+    for (int j = 0; j < KC; ++j) {
+      const double2 x = reinterpret_cast<const double2*>(p)[j];
+      a[j][0] = pdup(x.x);
+      a[j][1] = pdup(x.y);
+    }
+  }
+}
+
 // Loads the Cv' pairs of record l.
 template <int W, typename R>
 __device__ __forceinline__ void load_cv_pairs(const unsigned char* s_cv, int l,
@@ -498,10 +585,13 @@ __device__ __forceinline__ void grid_item(const SweepArgs& a, const R* __restric
       for (int h = 0; h < RH; ++h) loR[j][h] = loI[j][h] = pzero<P>();
   }
   const int myslot = lane & (L::PS - 1);
+  zero_bytes(s_cv + 32 * L::CVS * sizeof(R), L::CVS * sizeof(R), lane);
+  zero_bytes(s_a + 32 * L::AP, L::AP, lane);
   // software pipeline over 32-record windows of the item (window k = records
   // rb + 32k .. rb + 32k + 31, lane l holding record rb + 32k + l): while window k is
   // processed, the visibilities of window k+1 and the records of window k+2 are in flight
   const int rb = off[item.r0], rend = off[item.r1];
+  int pend = pair_ends(off, item, 0, lane);
   int wbase = rb, cstart = rb;
   Fetch<R> f0{}, f1{}, f2{};
   fetch_rec(rb, rend, f0);
@@ -515,7 +605,8 @@ __device__ __forceinline__ void grid_item(const SweepArgs& a, const R* __restric
       const int gb = g0 + gp * kD;
       if (gb < nrows) {
         const int row0 = item.r0 + gb;
-        const int re = off[min(row0 + kD, item.r1)];
+        if (gb > 0 && (gb & 63) == 0) pend = pair_ends(off, item, gb >> 6, lane);
+        const int re = __shfl_sync(0xffffffffu, pend, (gb & 63) >> 1);
         while (cstart < re) {
           // chunk: records [cstart, ce) of window wbase, staged by lanes cstart - wbase ..
           const int ce = min(re, wbase + 32);
@@ -524,8 +615,7 @@ __device__ __forceinline__ void grid_item(const SweepArgs& a, const R* __restric
           if (mine) {
             int ou, ov;
             R fu, fv;
-            table_coord<R, EXT>(Wp, a.Ms, a.interp, f0.rc.su, ou, fu);
-            table_coord<R, EXT>(Wp, a.Ms, a.interp, f0.rc.sv, ov, fv);
+            record_coords<R, EXT>(a, f0.rc, ou, fu, ov, fv);
             stage_grid<W, R, EXT>(tab, Wp, a.interp, ou, fu, ov, fv, rec_row(f0.rc.rx) - row0, xrel,
                                   f0.v.x * f0.wt, f0.v.y * f0.wt, s_cv, s_a, lane);
           }
@@ -535,22 +625,17 @@ __device__ __forceinline__ void grid_item(const SweepArgs& a, const R* __restric
           while (M) {
             const int l1 = __ffs(M) - 1;
             M &= M - 1u;
-            const bool two = M != 0u;
-            const int l2 = two ? __ffs(M) - 1 : l1;
-            if (two) M &= M - 1u;
+            const int l2 = M ? __ffs(M) - 1 : 32;  // record 32 is zero
+            M &= M - 1u;
             P c1[NPR], c2[NPR];
             load_cv_pairs<W, R>(s_cv, l1, c1);
             load_cv_pairs<W, R>(s_cv, l2, c2);
-            R a1r[KC], a1i[KC], a2r[KC], a2i[KC];
-            load_cols<R, KC>(reinterpret_cast<const C2*>(s_a + (l1 * (L::PS + 1) + myslot) * L::SA), a1r, a1i);
-            load_cols<R, KC>(reinterpret_cast<const C2*>(s_a + (l2 * (L::PS + 1) + myslot) * L::SA), a2r, a2i);
-            if (!two) {
-#pragma unroll
-              for (int j = 0; j < KC; ++j) a2r[j] = a2i[j] = R(0);
-            }
+            P a1[KC][2], a2[KC][2];
+            load_slot<R, KC>(s_a + l1 * L::AP + myslot * L::SA, a1);
+            load_slot<R, KC>(s_a + l2 * L::AP + myslot * L::SA, a2);
 #pragma unroll
             for (int j = 0; j < KC; ++j) {
-              const P d1r = pdup(a1r[j]), d1i = pdup(a1i[j]), d2r = pdup(a2r[j]), d2i = pdup(a2i[j]);
+              const P d1r = a1[j][0], d1i = a1[j][1], d2r = a2[j][0], d2i = a2[j][1];
 #pragma unroll
               for (int m = 0; m < NPR; ++m) {
                 const int h = (gp + m) % RH;
@@ -682,27 +767,37 @@ __device__ __forceinline__ void degrid_item(const SweepArgs& a, const R* __restr
   const int col0 = item.strip * S + KC * lane;
   const int nrows = item.r1 - item.r0;
   // ring pair h holds grid rows item.r0 + 2h' and + 1 (h' = h mod RH) of the lane's columns;
-  // rows 0 .. TP - 3 are loaded up front, each group loads the pair that completes its window
+  // rows 0 .. TP - 3 are loaded up front; each group moves the pair that completes its
+  // window into the ring (loaded during the previous group) and loads the next group's
   P gR[KC][RH], gI[KC][RH];
-  auto load_pair = [&](int x, int h) {  // relative rows x, x + 1 into ring pair h
-    R r0[KC], i0[KC], r1[KC], i1[KC];
-    load_cols<R, KC>(G + static_cast<size_t>((item.r0 + x) % N) * N + col0, r0, i0);
-    load_cols<R, KC>(G + static_cast<size_t>((item.r0 + x + 1) % N) * N + col0, r1, i1);
+  R nr0[KC], ni0[KC], nr1[KC], ni1[KC];  // the next window-completing pair, in flight
+  auto fetch_pair = [&](int x) {  // relative rows x, x + 1
+    load_cols<R, KC>(G + static_cast<size_t>((item.r0 + x) % N) * N + col0, nr0, ni0);
+    load_cols<R, KC>(G + static_cast<size_t>((item.r0 + x + 1) % N) * N + col0, nr1, ni1);
+  };
+  auto put_pair = [&](int h) {
 #pragma unroll
     for (int j = 0; j < KC; ++j) {
       if constexpr (sizeof(R) == 4) {
-        gR[j][h] = f2pack(r0[j], r1[j]);
-        gI[j][h] = f2pack(i0[j], i1[j]);
+        gR[j][h] = f2pack(nr0[j], nr1[j]);
+        gI[j][h] = f2pack(ni0[j], ni1[j]);
       } else {
-        gR[j][h] = make_double2(r0[j], r1[j]);
-        gI[j][h] = make_double2(i0[j], i1[j]);
+        gR[j][h] = make_double2(nr0[j], nr1[j]);
+        gI[j][h] = make_double2(ni0[j], ni1[j]);
       }
     }
   };
 #pragma unroll
-  for (int h = 0; h < NPR - 1; ++h) load_pair(2 * h, h);
+  for (int h = 0; h < NPR - 1; ++h) {
+    fetch_pair(2 * h);
+    put_pair(h);
+  }
+  fetch_pair(2 * (NPR - 1));
   const int myslot = lane & (L::PS - 1);
+  zero_bytes(s_cv + 32 * L::CVS * sizeof(R), L::CVS * sizeof(R), lane);
+  zero_bytes(s_u + 32 * L::UP, L::UP, lane);
   const int rb = off[item.r0], rend = off[item.r1];
+  int pend = pair_ends(off, item, 0, lane);
   int wbase = rb, cstart = rb;
   Rec rc0{0u, 0, 0u, 0u}, rc1{0u, 0, 0u, 0u}, rc2{0u, 0, 0u, 0u};
   if (rb + lane < rend) rc0 = recs[rb + lane];
@@ -714,8 +809,10 @@ __device__ __forceinline__ void degrid_item(const SweepArgs& a, const R* __restr
       const int gb = g0 + gp * kD;
       if (gb < nrows) {
         const int row0 = item.r0 + gb;
-        load_pair(gb + 2 * (NPR - 1), (gp + NPR - 1) % RH);
-        const int re = off[min(row0 + kD, item.r1)];
+        put_pair((gp + NPR - 1) % RH);
+        fetch_pair(gb + 2 * NPR);
+        if (gb > 0 && (gb & 63) == 0) pend = pair_ends(off, item, gb >> 6, lane);
+        const int re = __shfl_sync(0xffffffffu, pend, (gb & 63) >> 1);
         while (cstart < re) {
           const int ce = min(re, wbase + 32);
           const bool mine = lane >= cstart - wbase && lane < ce - wbase;
@@ -723,8 +820,7 @@ __device__ __forceinline__ void degrid_item(const SweepArgs& a, const R* __restr
           if (mine) {
             int ou, ov;
             R fu, fv;
-            table_coord<R, EXT>(Wp, a.Ms, a.interp, rc0.su, ou, fu);
-            table_coord<R, EXT>(Wp, a.Ms, a.interp, rc0.sv, ov, fv);
+            record_coords<R, EXT>(a, rc0, ou, fu, ov, fv);
             stage_degrid<W, R, EXT>(tab, Wp, a.interp, ou, fu, ov, fv, rec_row(rc0.rx) - row0, xrel, s_cv, s_u,
                                     lane);
           }
@@ -735,15 +831,15 @@ __device__ __forceinline__ void degrid_item(const SweepArgs& a, const R* __restr
             const int l1 = __ffs(M) - 1;
             M &= M - 1u;
             const bool two = M != 0u;
-            const int l2 = two ? __ffs(M) - 1 : l1;
-            if (two) M &= M - 1u;
+            const int l2 = two ? __ffs(M) - 1 : 32;  // record 32 is zero
+            M &= M - 1u;
             P c1[NPR], c2[NPR];
             load_cv_pairs<W, R>(s_cv, l1, c1);
             load_cv_pairs<W, R>(s_cv, l2, c2);
             R u1[KC], u2[KC];
             {
-              const unsigned char* p1 = s_u + (l1 * (L::PS + 1) + myslot) * L::SU;
-              const unsigned char* p2 = s_u + (l2 * (L::PS + 1) + myslot) * L::SU;
+              const unsigned char* p1 = s_u + l1 * L::UP + myslot * L::SU;
+              const unsigned char* p2 = s_u + l2 * L::UP + myslot * L::SU;
               if constexpr (sizeof(R) == 4 && KC == 2) {
                 const float2 x1 = *reinterpret_cast<const float2*>(p1), x2 = *reinterpret_cast<const float2*>(p2);
                 u1[0] = x1.x;
@@ -777,8 +873,8 @@ __device__ __forceinline__ void degrid_item(const SweepArgs& a, const R* __restr
             o1.y = p1i;
             o2.x = p2r;
             o2.y = p2i;
-            *reinterpret_cast<C2*>(s_p + (l1 * (L::PS + 1) + myslot) * L::SP) = o1;
-            if (two) *reinterpret_cast<C2*>(s_p + (l2 * (L::PS + 1) + myslot) * L::SP) = o2;
+            *reinterpret_cast<C2*>(s_p + l1 * L::PP + myslot * L::SP) = o1;
+            if (two) *reinterpret_cast<C2*>(s_p + l2 * L::PP + myslot * L::SP) = o2;
           }
           __syncwarp();
           if (mine) {
@@ -789,7 +885,7 @@ __device__ __forceinline__ void degrid_item(const SweepArgs& a, const R* __restr
             for (int m = 0; m < L::NL; ++m) {
               const int Ln = L0 + m;
               if (Ln >= 0 && Ln <= 31 && Ln <= L1) {
-                const C2 p = *reinterpret_cast<const C2*>(s_p + (lane * (L::PS + 1) + (Ln & (L::PS - 1))) * L::SP);
+                const C2 p = *reinterpret_cast<const C2*>(s_p + lane * L::PP + (Ln & (L::PS - 1)) * L::SP);
                 vr += p.x;
                 vi += p.y;
               }
