@@ -17,6 +17,9 @@ Two further workloads print their own line (not the headline):
                        (64 channels x 384 samples over 0.95-1.05 GHz), 4096^2 grid, W = 8:
                        forward + backward with all channels in one plan against one plan
                        per channel.
+  --workload precision float64 sweeps on the 4.1M-visibility tracks (Section 5.2): W = 7 with linear
+                       (M_s = 1000) and cubic (M_s = 20000) tables and with the direct calculation of
+                       the weights, W = 14 with a cubic table; next to the float32 W = 7 sweeps.
   --workload large     high accuracy at scale: 128 antennas x 768 samples (8 h) x 32
                        channels = 2.0e8 visibilities, 8192^2 grid, W = 12: float32 gridding
                        with plain and with compensated (two-float) accumulation, errors
@@ -54,7 +57,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="tracks", choices=["tracks", "channels", "autograd", "large"])
+    ap.add_argument("--workload", default="tracks", choices=["tracks", "channels", "autograd", "large", "precision"])
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=0,
@@ -966,6 +969,55 @@ def run_large(args):
     print(json.dumps(line), flush=True)
 
 
+def run_precision(args):
+    """Sweep throughput of the float64 path against the float32 one (Section 5.2: the direct
+    calculation of the weights against table lookups, and the W = 14 double-precision
+    design), on the 4.1M-visibility tracks; L2 flushed before every timed launch."""
+    import torch
+    from paper_1906_07102_gb300 import lmg
+    torch.cuda.set_device(0)
+    uv, dl, vis, model = make_inputs()
+    nv = uv.shape[0]
+    dev = torch.device("cuda", 0)
+    uv_d = torch.from_numpy(uv).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    cases = [("c64", 7, "linear", 1000), ("c128", 7, "linear", 1000), ("c128", 7, "cubic", 20000),
+             ("c128", 7, "direct", 4), ("c128", 14, "cubic", 20000)]
+    out = []
+    ref = {}
+    for dt, W, interp, Ms in cases:
+        tab = lmg.Table(W, 0.5, Ms, interp)
+        plan = lmg.Plan(tab, WORKLOAD["n_image"], dl, nv, dt)
+        plan.bin(uv_d)
+        cd = torch.complex64 if dt == "c64" else torch.complex128
+        v = torch.from_numpy(vis.astype(np.complex64 if dt == "c64" else np.complex128)).to(dev)
+        g = torch.empty((WORKLOAD["N"], WORKLOAD["N"]), dtype=cd, device=dev)
+        vo = torch.empty_like(v)
+        reps = max(3, min(args.steps, 10))
+        tg = _events_ms(lambda: plan.grid(v, out=g), reps, flush, stream, torch)
+        plan.grid(v, out=g)
+        td = _events_ms(lambda: plan.degrid(g, out=vo), reps, flush, stream, torch)
+        plan.degrid(g, out=vo)
+        torch.cuda.synchronize()
+        gi = g.cpu().numpy()[::64, ::64].astype(np.complex128)
+        key = (W,)
+        row = {"dtype": dt, "W": W, "interp": interp, "oversample": Ms, "grid_ms": tg, "degrid_ms": td,
+               "grid_degrid_mvis_s": nv / ((tg + td) * 1e-3) / 1e6}
+        if key in ref:  # agreement of the grid with the first float64 case of the same W
+            r = ref[key]
+            row["grid_rel_diff_vs_" + r[0]] = float(np.sqrt(np.mean(np.abs(gi - r[1]) ** 2) / np.mean(np.abs(r[1]) ** 2)))
+        elif dt == "c128":
+            ref[key] = (f"{interp}{Ms}", gi)
+        out.append(row)
+        del plan, g, vo, v
+        torch.cuda.empty_cache()
+    line = {"workload": "precision", "config": {"workload": WORKLOAD_NAME + " (values used as complex128 for the "
+                                                                        "float64 rows)"},
+            "unit": "ms per launch pass; Mvis/s", "cases": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -976,6 +1028,8 @@ def main():
         run_autograd(args)
     elif args.workload == "large":
         run_large(args)
+    elif args.workload == "precision":
+        run_precision(args)
     else:
         run_native(args)
 

@@ -227,14 +227,19 @@ __global__ void k_bin_scatter(const double* __restrict__ uv, double scale2, cons
         if (xr + W > strip_w) g2[u] = ((strip + 1) % n_strips) * N + pair_row;
       }
     }
+    // offsets of the pair's two rows and of the next pair (g is even: one 8-byte load and one
+    // 4-byte load per record)
     int o1[kCountIlp][3], o2[kCountIlp][3];
 #pragma unroll
     for (int u = 0; u < kCountIlp; ++u) {
-#pragma unroll
-      for (int e = 0; e < 3; ++e) {
-        o1[u][e] = g1[u] >= 0 ? offsets[g1[u] + e] : 0;
-        o2[u][e] = g2[u] >= 0 ? offsets[g2[u] + e] : 0;
-      }
+      const int2 a1 = g1[u] >= 0 ? *reinterpret_cast<const int2*>(offsets + g1[u]) : make_int2(0, 0);
+      const int2 a2 = g2[u] >= 0 ? *reinterpret_cast<const int2*>(offsets + g2[u]) : make_int2(0, 0);
+      o1[u][0] = a1.x;
+      o1[u][1] = a1.y;
+      o1[u][2] = g1[u] >= 0 ? offsets[g1[u] + 2] : 0;
+      o2[u][0] = a2.x;
+      o2[u][1] = a2.y;
+      o2[u][2] = g2[u] >= 0 ? offsets[g2[u] + 2] : 0;
     }
 #pragma unroll
     for (int u = 0; u < kCountIlp; ++u) {
