@@ -121,6 +121,11 @@ __device__ __forceinline__ unsigned long long f2fma(unsigned long long a, unsign
 __device__ __forceinline__ void red_add(float2* p, float2 v) {
   asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(v.x), "f"(v.y) : "memory");
 }
+// two complex64 values (16 bytes, 16-byte aligned) in one vector reduction
+__device__ __forceinline__ void red_add2(float2* p, float2 a, float2 b) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y)
+               : "memory");
+}
 __device__ __forceinline__ void red_add(double2* p, double2 v) {
   atomicAdd(&p->x, v.x);
   atomicAdd(&p->y, v.y);

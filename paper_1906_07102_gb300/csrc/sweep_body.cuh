@@ -734,12 +734,17 @@ __device__ __forceinline__ void spill_item(const Item* __restrict__ items, int n
 #pragma unroll
   for (int j = 0; j < kMaxRows; ++j)
     if (j < W - 1) {
+      typename Cplx<R>::T* dst = g + static_cast<size_t>((item.r1 + j) % N) * N;
+      if constexpr (sizeof(R) == 4 && KC == 2) {
+        red_add2(dst, make_float2(vr[j][0], vi[j][0]), make_float2(vr[j][1], vi[j][1]));
+      } else {
 #pragma unroll
-      for (int c = 0; c < KC; ++c) {
-        typename Cplx<R>::T v;
-        v.x = vr[j][c];
-        v.y = vi[j][c];
-        red_add(g + static_cast<size_t>((item.r1 + j) % N) * N + c, v);
+        for (int c = 0; c < KC; ++c) {
+          typename Cplx<R>::T v;
+          v.x = vr[j][c];
+          v.y = vi[j][c];
+          red_add(dst + c, v);
+        }
       }
     }
 }

@@ -327,6 +327,46 @@ def test_support_widths_fp64_kernel_exact(W):
         assert np.abs(vd - vref).max() <= 1e-12 * np.abs(vref).max(), interp
 
 
+@pytest.mark.parametrize("W", list(range(1, 17)))
+def test_support_widths_fp32_two_columns_per_lane(W):
+    """complex64 lanes own two columns of 64-column strips, and the slots a record fills
+    depend on W and on the parity of its start column: every W = 1..16 with every lookup,
+    against the float64 oracle on the same closed-form table, per element within 1e-5 of the
+    largest value (the float32 target)."""
+    N, n_img, Ms, nvis = 128, 64, 64, 1500
+    uv, dl = disk_case(nvis, N, seed=100 + W)
+    vis = S.complex_normal(nvis, 100 + W)
+    T = caller_table(W, Ms)
+    op = oracle_plan(uv, dl, W, N, single=False)
+    Gm = S.random_image(N, 200 + W)
+    for interp in ("nearest", "linear", "quadratic", "cubic"):
+        p = gpu_plan(W, 0.5, Ms, interp, n_img, dl, nvis, "c64", values=T)
+        p.bin(to_dev(uv, torch.float64))
+        g = p.grid(to_dev(vis.astype(np.complex64), torch.complex64)).cpu().numpy()
+        ref = I.grid(op, T, Ms, INTERP[interp], vis.astype(np.complex64).astype(np.complex128))
+        assert np.abs(g - ref).max() <= 1e-5 * np.abs(ref).max(), interp
+        vd = p.degrid(to_dev(Gm.astype(np.complex64), torch.complex64)).cpu().numpy()
+        vref = I.degrid(op, T, Ms, INTERP[interp], Gm.astype(np.complex64).astype(np.complex128))
+        assert np.abs(vd - vref).max() <= 1e-5 * np.abs(vref).max(), interp
+
+
+@pytest.mark.parametrize("nvis", [0, 1, 33, 4097])
+def test_ragged_counts_fp32(nvis):
+    N, n_img, W, Ms = 128, 64, 7, 100
+    uv, dl = disk_case(max(nvis, 1), N, seed=300 + nvis)
+    uv = uv[:nvis].reshape(-1, 2)
+    vis = S.complex_normal(nvis, 300 + nvis).astype(np.complex64)
+    T = caller_table(W, Ms)
+    p = gpu_plan(W, 0.5, Ms, "linear", n_img, dl, max(nvis, 1), "c64", values=T)
+    p.bin(to_dev(uv, torch.float64))
+    g = p.grid(to_dev(vis, torch.complex64)).cpu().numpy()
+    ref = I.grid(oracle_plan(uv, dl, W, N, single=False), T, Ms, 1, vis.astype(np.complex128))
+    if nvis == 0:
+        assert not np.any(g)
+    else:
+        assert np.abs(g - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
 @pytest.mark.parametrize("nvis", [0, 1, 31, 33, 4097])
 def test_ragged_counts(nvis):
     N, n_img, W, Ms = 128, 64, 7, 100
