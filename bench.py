@@ -2,7 +2,9 @@
 
 One step = the whole hot path on one batch of visibilities: bin the positions, grid,
 FFT (+i), correct and crop to the dirty image; pad and correct a model image, FFT (-i),
-degrid to predicted visibilities. Workload: 64-antenna Earth-rotation tracks (6 h,
+degrid to predicted visibilities. The model's pad and transform, which do not depend on the
+positions, run on a second stream while the positions are binned and gridded, and the
+degridding runs on a third while the dirty image is transformed and cropped. Workload: 64-antenna Earth-rotation tracks (6 h,
 2048 samples, 1.4 GHz; 4,128,768 visibilities), 4096^2 grid, 2048^2 image (x0 = 0.5),
 W = 7, linear table at M_s = 1000, complex64.
 
@@ -382,6 +384,54 @@ def accuracy(uv, dl, vis, model, img, pv):
             "sample": "24 random pixels of the 2048^2 dirty image; 2000 random predicted visibilities"}
 
 
+class OverlappedStep:
+    """One step of the hot path through the public calls, with work that does not depend on
+    other work on separate streams: the prediction's pad + correct of the model (into a
+    workspace grid, zero outside the kept field) and its model transform (kept rows, then
+    every column) run on a side stream from the step's start, concurrently with the binning
+    and gridding on the caller's stream; after the gridding, the degridding of the
+    transformed model runs on a third stream while the caller's stream transforms and crops
+    the dirty image; the caller's stream ends the step when both are done. Nothing of step
+    k + 1 starts on any stream before step k has ended on the caller's stream.
+    Measured on the 4.1M-visibility workload: 0.982 ms per step against 1.024 ms with the
+    same calls in series (1.008 ms with the model transform alone overlapped)."""
+
+    def __init__(self, plan, N, dev):
+        import torch
+        self.torch = torch
+        self.plan = plan
+        self.side = torch.cuda.Stream(device=dev)
+        self.side2 = torch.cuda.Stream(device=dev)
+        self.work = torch.empty((N, N), dtype=torch.complex64, device=dev)
+        self.model_grid = torch.empty((N, N), dtype=torch.complex64, device=dev)
+        self.start = torch.cuda.Event()
+        self.model_ready = torch.cuda.Event()
+        self.gridded = torch.cuda.Event()
+        self.predicted = torch.cuda.Event()
+
+    def __call__(self, uv, vis, model, img, pv, main, img_ready=None):
+        torch, plan = self.torch, self.plan
+        self.start.record(main)
+        self.side.wait_event(self.start)
+        with torch.cuda.stream(self.side):
+            plan.pad_correct(model, out=self.model_grid)
+            plan.fft(self.model_grid, "model", pruned=True)
+            self.model_ready.record(self.side)
+        plan.bin(uv)
+        plan.grid(vis, out=self.work)
+        self.gridded.record(main)
+        self.side2.wait_event(self.gridded)
+        self.side2.wait_event(self.model_ready)
+        with torch.cuda.stream(self.side2):
+            plan.degrid(self.model_grid, out=pv)
+            self.predicted.record(self.side2)
+        plan.fft(self.work, "image", pruned=True)
+        plan.crop_correct(self.work, out=img)
+        if img_ready is not None:
+            img_ready.record(main)
+        main.wait_event(self.predicted)
+
+
 def run_native(args):
     import torch
     rank, world, local = dist_env()
@@ -406,10 +456,10 @@ def run_native(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
+    ostep = OverlappedStep(plan, w["N"], dev)
+
     def step():
-        plan.bin(uv_d)
-        plan.dirty_image(vis_d, out=img_d)
-        plan.predict_vis(model_d, out=pv_d)
+        ostep(uv_d, vis_d, model_d, img_d, pv_d, stream)
 
     if args.profile_steps:
         for _ in range(args.profile_steps):
@@ -531,11 +581,8 @@ def run_native(args):
             stream.wait_event(up[b])
             stream.wait_event(down[b])
             d = bufs[b]
-            plan.bin(d["uv"])
-            plan.dirty_image(d["vis"], out=d["img"])
             img_ready = ev()
-            img_ready.record(stream)
-            plan.predict_vis(d["model"], out=d["pv"])
+            ostep(d["uv"], d["vis"], d["model"], d["img"], d["pv"], stream, img_ready)
             used[b].record(stream)
             s_out.wait_event(img_ready)
             with torch.cuda.stream(s_out):
