@@ -334,16 +334,16 @@ def sweep_sources_sha256():
     return h.hexdigest()
 
 
-def traffic_record():
-    """DRAM traffic of the gridding pass from the committed ncu summary, if it was taken
-    on the current sweep sources."""
-    p = os.path.join(ROOT, "profiles", "grid_sweep_config2_traffic.json")
+def traffic_record(pass_name):
+    """DRAM traffic per launch of the gridding ("grid") or degridding ("degrid") sweep from
+    the committed ncu summary, if it was taken on the current sweep sources."""
+    p = os.path.join(ROOT, "profiles", "sweeps_config2_traffic.json")
     try:
         with open(p) as f:
             rec = json.load(f)
         if rec.get("sweep_sources_sha256") != sweep_sources_sha256():
             return None
-        return float(rec["traffic_bytes_per_launch"])
+        return float(rec[pass_name]["traffic_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
         return None
 
@@ -622,7 +622,7 @@ def run_native(args):
                        else "k_degrid_sweep with its output zeroing (degridding pass)"),
             "bound": "hbm" if t_hbm >= t_alu else "alu", "achieved": achieved,
             "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic_record() if dom == "grid" else None,
+            "traffic": traffic_record(dom),
             "algorithmic_bytes": pass_bytes, "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs, burst)",
             "fp32_side": {"flops": pass_flops, "peak_tflops": fp32, "achieved_tflops": pass_flops / t_dom / 1e12,
                           "frac": pass_flops / t_dom / 1e12 / fp32,
