@@ -135,7 +135,7 @@ int lmg_correction_export(const lmg_table* t, int64_t n_image, int single_precis
 
 /* lmg_plan_create -- device state for imaging with one table at one image size.
  *   n_image      kept image side (pixels); N = n_image / x0 must be an even integer,
- *                a multiple of 32, and at least 64
+ *                a multiple of 64 (LMG_C64) or 32 (LMG_C128), and at least 64
  *   pixel_scale  image pixel size in radians (u_cells = u * N * pixel_scale)
  *   max_vis      capacity: the largest nvis later passed to lmg_plan_bin (>= 1)
  *   dtype        LMG_C64 or LMG_C128
@@ -156,12 +156,23 @@ int lmg_plan_create_ex(const lmg_table* t, int64_t n_image, double pixel_scale,
 int lmg_plan_free(lmg_plan* p);
 
 /* lmg_plan_bin -- bin visibility positions for gridding and degridding (support rule of
- * Eq. 6; sort into 32-column strips by support-start row; balanced work items). Must be
- * called before lmg_grid / lmg_degrid / lmg_dirty_image / lmg_predict_vis and again
- * whenever the positions change. uv: device float64 [nvis][2] in wavelengths,
- * 0 <= nvis <= max_vis; read by two kernels of this call (counting, then placing the
- * records), so it must stay unchanged until the stream has run them. Allocates nothing. */
+ * Eq. 6; sort into strips of 64 columns (LMG_C64) or 32 columns (LMG_C128) by support-start
+ * row; balanced work items). Must be called before lmg_grid / lmg_degrid / lmg_dirty_image /
+ * lmg_predict_vis and again whenever the positions change. uv: device float64 [nvis][2] in
+ * wavelengths, 16-byte aligned, 0 <= nvis <= max_vis; read by two kernels of this call
+ * (counting, then placing the records), so it must stay unchanged until the stream has run
+ * them. Allocates nothing. */
 int lmg_plan_bin(lmg_plan* p, const double* uv, int64_t nvis, void* stream);
+
+/* lmg_plan_bin_tracks -- lmg_plan_bin for positions stored sample-major: visibility
+ * k = t * tracks + b is sample t of track b (one baseline of one channel), as a correlator
+ * writes one integration of every baseline after another; a last partial sample row is
+ * allowed (nvis need not be a multiple of tracks). Each binning thread follows one track
+ * over 32 consecutive samples, and samples that share a bucket take one counter update and
+ * one offset lookup per run instead of one per record. The binning is the same for any
+ * tracks >= 1 (the order of the records within a bucket, and so the rounding order of the
+ * sums, may differ); the hint only changes the cost. LMG_EINVAL for tracks < 1. */
+int lmg_plan_bin_tracks(lmg_plan* p, const double* uv, int64_t nvis, int64_t tracks, void* stream);
 
 /* lmg_plan_dropped -- number of positions dropped by the last lmg_plan_bin (not finite
  * or 2^30 cells or more from the origin). Synchronises the given stream. */
@@ -280,10 +291,11 @@ void* lmg_work_grid(lmg_plan* p);
  * a real-time pipeline that must not allocate while it runs. The paper has no
  * counterpart; this is a deployment variant of the existing path.
  *
- * All working memory (bucket ranks, records, bucket counts, work items, spill rows and the
- * float32 copy of the table) lives in one fixed-size __device__ array of this library,
- * about 16 MB, which every GPU that loads the library holds until the process exits.
- * Limits: nvis <= LMG_STATIC_MAX_VIS, grid N = n_image / x0 a multiple of 32 in
+ * All working memory (decoded positions and ranks, records, bucket counts, work items,
+ * spill rows and the float32 copy of the table) lives in one fixed-size __device__ array
+ * of this library, about 21 MB, which every GPU that loads the library holds until the
+ * process exits.
+ * Limits: nvis <= LMG_STATIC_MAX_VIS, grid N = n_image / x0 a multiple of 64 in
  * [64, LMG_STATIC_MAX_N], table oversample <= LMG_STATIC_MAX_OVERSAMPLE; larger sizes
  * return LMG_EINVAL with a message and do nothing.
  *   t            table (host object from lmg_kernel_table or lmg_table_from_values)

@@ -85,7 +85,7 @@ namespace lmg {
 
 void free_plan(lmg_plan* p) {
   if (!p) return;
-  void* ptrs[] = {p->d_table, p->d_h, p->hist, p->offsets, p->rank, p->partial, p->recs,
+  void* ptrs[] = {p->d_table, p->d_h, p->hist, p->offsets, p->pos, p->rank2, p->partial, p->recs,
                   p->items, p->counters, p->spill, p->frac, p->work, p->model};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -309,7 +309,8 @@ int plan_create(const lmg_table* t, int64_t n_image, double pixel_scale, int64_t
   if ((rc = dalloc(reinterpret_cast<unsigned char**>(&p->d_table), tab_bytes.size(), "table")) ||
       (rc = dalloc(reinterpret_cast<unsigned char**>(&p->d_h), h_bytes.size(), "correction")) ||
       (rc = dalloc(&p->hist, size_t(L), "histogram")) ||
-      (rc = dalloc(&p->offsets, size_t(L) + 1, "offsets")) || (rc = dalloc(&p->rank, size_t(max_vis), "ranks")) ||
+      (rc = dalloc(&p->offsets, size_t(L) + 1, "offsets")) || (rc = dalloc(&p->pos, size_t(max_vis), "positions")) ||
+      (rc = dalloc(&p->rank2, size_t(max_vis), "ranks")) ||
       (rc = dalloc(&p->partial, size_t(p->nchunks), "scan")) || (rc = dalloc(&p->recs, size_t(2 * max_vis), "records")) ||
       (rc = dalloc(&p->items, size_t(p->item_cap), "items")) || (rc = dalloc(&p->counters, kNumCounters, "counters")) ||
       (rc = dalloc(reinterpret_cast<unsigned char**>(&p->spill), size_t(p->item_cap) * ring_slots(p->W) * strip * c2, "spill")) ||
@@ -391,9 +392,10 @@ int plan_create(const lmg_table* t, int64_t n_image, double pixel_scale, int64_t
   return LMG_OK;
 }
 
-int plan_bin(lmg_plan* p, const double* uv, int64_t nvis, cudaStream_t st) {
+int plan_bin(lmg_plan* p, const double* uv, int64_t nvis, cudaStream_t st, int64_t tracks) {
   BinArgs a{};
   a.uv = uv;
+  a.tracks = tracks;
   a.nvis = nvis;
   a.scale2 = p->scale2;
   a.W = p->W;
@@ -406,7 +408,8 @@ int plan_bin(lmg_plan* p, const double* uv, int64_t nvis, cudaStream_t st) {
   a.max_blocks = p->sms * 8;
   a.hist = p->hist;
   a.offsets = p->offsets;
-  a.rank = p->rank;
+  a.pos = p->pos;
+  a.rank2 = p->rank2;
   a.partial = p->partial;
   a.recs = p->recs;
   a.items = p->items;
@@ -542,6 +545,16 @@ int lmg_plan_bin(lmg_plan* p, const double* uv, int64_t nvis, void* stream) {
   if (nvis > 0 && !uv) return set_error(LMG_EINVAL, "uv is NULL");
   if (reinterpret_cast<uintptr_t>(uv) % 16 != 0) return set_error(LMG_EINVAL, "uv must be 16-byte aligned");
   return plan_bin(p, uv, nvis, static_cast<cudaStream_t>(stream));
+}
+
+int lmg_plan_bin_tracks(lmg_plan* p, const double* uv, int64_t nvis, int64_t tracks, void* stream) {
+  clear_error();
+  if (!p) return set_error(LMG_EINVAL, "plan is NULL");
+  if (nvis < 0 || nvis > p->max_vis) return set_error(LMG_EINVAL, "nvis must be in [0, max_vis]");
+  if (nvis > 0 && !uv) return set_error(LMG_EINVAL, "uv is NULL");
+  if (tracks < 1) return set_error(LMG_EINVAL, "tracks must be >= 1");
+  if (reinterpret_cast<uintptr_t>(uv) % 16 != 0) return set_error(LMG_EINVAL, "uv must be 16-byte aligned");
+  return plan_bin(p, uv, nvis, static_cast<cudaStream_t>(stream), tracks);
 }
 
 int lmg_plan_dropped(lmg_plan* p, int64_t* dropped, void* stream) {

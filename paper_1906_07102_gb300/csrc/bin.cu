@@ -1,18 +1,22 @@
 // Binning of visibility positions (support rule of Eq. 6) into strips of 64 (complex64) or
-// 32 (complex128) columns sorted
-// by pairs of support-start rows, and balanced work items for the sweep kernels.
+// 32 (complex128) columns sorted by pairs of support-start rows, and balanced work items for
+// the sweep kernels.
 //
 // Pipeline (all on one stream, no host synchronisation):
 //   1. k_bin_count   per visibility: float64 product to cells, exact fixed-point support
 //                    rule, strip keys (one, or two when the support crosses into the next
-//                    strip); the bucket counter's returned value is the record's rank.
+//                    strip); the bucket counter's returned value is the record's rank. The
+//                    decoded position (cell, table coordinates, rank) is stored in one
+//                    16-byte entry per visibility, so that the next pass does no float64 or
+//                    fixed-point work (float64 runs at a small fraction of the float32 rate).
 //   2. scan          exclusive prefix sum of the bucket counts (strip-major, row-minor).
-//   3. k_bin_scatter positions recomputed from (u, v) (cheaper than storing and reloading
-//                    them), records of each pair of rows (2m, 2m+1) of a strip -- the row
-//                    group the sweeps stage together -- to the pair's range, dealt so that
-//                    any 32 consecutive records sample the whole pair (see dealt_position).
+//   3. k_bin_scatter records of each pair of rows (2m, 2m+1) of a strip -- the row group
+//                    the sweeps stage together -- to the pair's range, dealt so that any 32
+//                    consecutive records sample the whole pair (see dealt_position).
 //   4. k_make_items  per strip and block of rows: items holding about item_target records,
 //                    cut at even rows so that the sweeps' row groups are these pairs.
+// With a track layout (positions stored sample-major, k = t * tracks + b) passes 1 and 3
+// follow each track instead (k_bin_count_tracks, k_bin_scatter_tracks).
 #include <cuda_runtime.h>
 
 #include "device_common.cuh"
@@ -20,6 +24,14 @@
 
 namespace lmg {
 namespace {
+
+// i mod N in [0, N); positions inside the grid (the usual case) take no division.
+__device__ __forceinline__ int wrap_index(long long i, int N) {
+  if (static_cast<unsigned long long>(i) < static_cast<unsigned long long>(N)) return static_cast<int>(i);
+  long long r = i % N;
+  if (r < 0) r += N;
+  return static_cast<int>(r);
+}
 
 // Support start (grid indices, wrapped to [0, N)) and table coordinates of position p =
 // (u, v); false for a dropped position (product not finite or |u| N pixel_scale >= 2^30).
@@ -31,13 +43,25 @@ __device__ __forceinline__ bool vis_position(double2 p, double scale2, int W, in
   long long n0, m0;
   support_start(U, W, n0, vp.su);
   support_start(V, W, m0, vp.sv);
-  long long xi = (n0 + N / 2) % N;
-  long long yi = (m0 + N / 2) % N;
-  if (xi < 0) xi += N;
-  if (yi < 0) yi += N;
-  vp.x0 = static_cast<int>(xi);
-  vp.y0 = static_cast<int>(yi);
+  vp.x0 = wrap_index(n0 + N / 2, N);
+  vp.y0 = wrap_index(m0 + N / 2, N);
   return true;
+}
+
+// Strip of a support-start column and the column inside it (strip_w is a power of two).
+__device__ __forceinline__ int strip_of(int x0, int strip_w) { return x0 >> (__ffs(strip_w) - 1); }
+__device__ __forceinline__ int col_in_strip(int x0, int strip_w) { return x0 & (strip_w - 1); }
+__device__ __forceinline__ int next_strip(int strip, int n_strips) { return strip + 1 == n_strips ? 0 : strip + 1; }
+
+// The 16-byte position entry (N <= 65536: the cell indices take 16 bits each); w carries a
+// rank (>= 0) or -1 for a dropped position.
+__device__ __forceinline__ int4 pack_pos(const VisPos& vp, int w) {
+  const unsigned xy = static_cast<unsigned>(vp.x0) | (static_cast<unsigned>(vp.y0) << 16);
+  return make_int4(static_cast<int>(xy), static_cast<int>(vp.su), static_cast<int>(vp.sv), w);
+}
+__device__ __forceinline__ VisPos unpack_pos(int4 c) {
+  return VisPos{c.x & 0xffff, static_cast<int>(static_cast<unsigned>(c.x) >> 16), static_cast<unsigned>(c.y),
+                static_cast<unsigned>(c.z)};
 }
 
 // Pass 1: positions to grid cells (support rule), bucket keys, and each record's rank in
@@ -47,8 +71,8 @@ __device__ __forceinline__ bool vis_position(double2 p, double scale2, int W, in
 constexpr int kCountIlp = 4;
 
 __global__ void k_bin_count(const double* __restrict__ uv, long long nvis, double scale2, int W,
-                            int N, int n_strips, int strip_w, int2* __restrict__ rank, int* __restrict__ hist,
-                            int* __restrict__ counters, double2* __restrict__ frac) {
+                            int N, int n_strips, int strip_w, int4* __restrict__ pos, int* __restrict__ rank2,
+                            int* __restrict__ hist, int* __restrict__ counters, double2* __restrict__ frac) {
   const int lane = threadIdx.x & 31;  // for the dropped-position count
   const long long span = static_cast<long long>(blockDim.x) * kCountIlp;
   const long long stride = static_cast<long long>(gridDim.x) * span;
@@ -61,16 +85,16 @@ __global__ void k_bin_count(const double* __restrict__ uv, long long nvis, doubl
       const long long k = base + u * blockDim.x + threadIdx.x;
       key1[u] = key2[u] = -1;
       bad[u] = false;
-      vp[u] = VisPos{-1, 0, 0u, 0u};
+      vp[u] = VisPos{0, 0, 0u, 0u};
       if (k < nvis) {
         double2 dl = make_double2(0.0, 0.0);
         const bool ok = vis_position(reinterpret_cast<const double2*>(uv)[k], scale2, W, N, vp[u],
                                      frac != nullptr ? &dl : nullptr);
         if (frac != nullptr) frac[k] = dl;
         if (ok) {
-          const int strip = vp[u].x0 / strip_w;
+          const int strip = strip_of(vp[u].x0, strip_w);
           key1[u] = strip * N + vp[u].y0;
-          if ((vp[u].x0 % strip_w) + W > strip_w) key2[u] = ((strip + 1) % n_strips) * N + vp[u].y0;
+          if (col_in_strip(vp[u].x0, strip_w) + W > strip_w) key2[u] = next_strip(strip, n_strips) * N + vp[u].y0;
         } else {
           bad[u] = true;
         }
@@ -79,13 +103,16 @@ __global__ void k_bin_count(const double* __restrict__ uv, long long nvis, doubl
     int2 rk[kCountIlp];
 #pragma unroll
     for (int u = 0; u < kCountIlp; ++u) {
-      rk[u].x = key1[u] >= 0 ? atomicAdd(hist + key1[u], 1) : 0;
+      rk[u].x = key1[u] >= 0 ? atomicAdd(hist + key1[u], 1) : -1;
       rk[u].y = key2[u] >= 0 ? atomicAdd(hist + key2[u], 1) : 0;
     }
 #pragma unroll
     for (int u = 0; u < kCountIlp; ++u) {
       const long long k = base + u * blockDim.x + threadIdx.x;
-      if (k < nvis) rank[k] = rk[u];
+      if (k < nvis) {
+        pos[k] = pack_pos(vp[u], rk[u].x);
+        rank2[k] = rk[u].y;
+      }
       const unsigned nb = __popc(__ballot_sync(0xffffffffu, bad[u]));
       if (lane == 0 && nb) atomicAdd(counters + kCntBad, static_cast<int>(nb));
     }
@@ -194,37 +221,42 @@ __device__ __forceinline__ int dealt_position(int rho, int n) {
   return j * q + min(j, r) + rho / nc;
 }
 
-__global__ void k_bin_scatter(const double* __restrict__ uv, double scale2, const int2* __restrict__ rank,
-                              long long nvis, int W, int N, int n_strips, int strip_w,
-                              const int* __restrict__ offsets, Rec* __restrict__ recs) {
-  // kCountIlp visibilities per thread per iteration: their position, rank and offset loads
-  // are in flight together (the pass is bound by its random L2 requests and their latency).
-  // (u, v) and the ranks are read for the last time here: streaming loads (evict first)
+__global__ void k_bin_scatter(const int4* __restrict__ pos, const int* __restrict__ rank2, long long nvis, int W,
+                              int N, int n_strips, int strip_w, const int* __restrict__ offsets,
+                              Rec* __restrict__ recs) {
+  // kCountIlp visibilities per thread per iteration: their position and offset loads are in
+  // flight together (the pass is bound by its random L2 requests and their latency). The
+  // positions and ranks are read for the last time here: streaming loads (evict first)
   // leave the L2 to the offsets and the records being written.
   const long long span = static_cast<long long>(blockDim.x) * kCountIlp;
   const long long stride = static_cast<long long>(gridDim.x) * span;
   for (long long base = static_cast<long long>(blockIdx.x) * span; base < nvis; base += stride) {
     VisPos vp[kCountIlp];
-    int2 rk[kCountIlp];
+    int r1[kCountIlp];
 #pragma unroll
     for (int u = 0; u < kCountIlp; ++u) {
       const long long k = base + u * blockDim.x + threadIdx.x;
-      vp[u] = VisPos{-1, 0, 0u, 0u};
-      rk[u] = make_int2(0, 0);
+      r1[u] = -1;
+      vp[u] = VisPos{0, 0, 0u, 0u};
       if (k < nvis) {
-        rk[u] = __ldcs(rank + k);
-        vis_position(__ldcs(reinterpret_cast<const double2*>(uv) + k), scale2, W, N, vp[u]);
+        const int4 c = __ldcs(pos + k);
+        vp[u] = unpack_pos(c);
+        r1[u] = c.w;
       }
     }
-    int g1[kCountIlp], g2[kCountIlp];  // bucket pair bases (-1: none)
+    int g1[kCountIlp], g2[kCountIlp], r2[kCountIlp];  // bucket pair bases (-1: none)
 #pragma unroll
     for (int u = 0; u < kCountIlp; ++u) {
       g1[u] = g2[u] = -1;
-      if (vp[u].x0 >= 0) {
-        const int strip = vp[u].x0 / strip_w, xr = vp[u].x0 % strip_w;
+      r2[u] = 0;
+      if (r1[u] >= 0) {
+        const int strip = strip_of(vp[u].x0, strip_w), xr = col_in_strip(vp[u].x0, strip_w);
         const int pair_row = vp[u].y0 & ~1;
         g1[u] = strip * N + pair_row;
-        if (xr + W > strip_w) g2[u] = ((strip + 1) % n_strips) * N + pair_row;
+        if (xr + W > strip_w) {
+          g2[u] = next_strip(strip, n_strips) * N + pair_row;
+          r2[u] = __ldcs(rank2 + base + u * blockDim.x + threadIdx.x);
+        }
       }
     }
     // offsets of the pair's two rows and of the next pair (g is even: one 8-byte load and one
@@ -245,13 +277,163 @@ __global__ void k_bin_scatter(const double* __restrict__ uv, double scale2, cons
     for (int u = 0; u < kCountIlp; ++u) {
       if (g1[u] < 0) continue;
       const long long k = base + u * blockDim.x + threadIdx.x;
-      const int odd = vp[u].y0 & 1, xr = vp[u].x0 % strip_w;
+      const int odd = vp[u].y0 & 1, xr = col_in_strip(vp[u].x0, strip_w);
       // row pair (y0 & ~1, y0 | 1) of the strip: [offsets[g], offsets[g + 2])
-      recs[o1[u][0] + dealt_position((odd ? o1[u][1] - o1[u][0] : 0) + rk[u].x, o1[u][2] - o1[u][0])] =
+      recs[o1[u][0] + dealt_position((odd ? o1[u][1] - o1[u][0] : 0) + r1[u], o1[u][2] - o1[u][0])] =
           Rec{static_cast<unsigned>(k), rec_pack(vp[u].y0, xr), vp[u].su, vp[u].sv};
       if (g2[u] >= 0)
-        recs[o2[u][0] + dealt_position((odd ? o2[u][1] - o2[u][0] : 0) + rk[u].y, o2[u][2] - o2[u][0])] =
+        recs[o2[u][0] + dealt_position((odd ? o2[u][1] - o2[u][0] : 0) + r2[u], o2[u][2] - o2[u][0])] =
             Rec{static_cast<unsigned>(k), rec_pack(vp[u].y0, xr - strip_w), vp[u].su, vp[u].sv};
+    }
+  }
+}
+
+// Track-ordered binning. With the positions stored sample-major (k = t * tracks + b: one
+// sample of every track, then the next sample), thread g follows track b = g mod tracks over
+// kTrackChunk consecutive samples (chunk g / tracks); the lanes of a warp read neighbouring
+// tracks at the same sample, so the position loads stay coalesced. Along a track the support
+// moves by at most a few cells per sample and consecutive samples fall in the same bucket
+// (strip, row) in runs (5.9 samples on average on 6 h Earth-rotation tracks with 64-column
+// strips). The counting pass takes one bucket atomic per run and stores the rank it returns
+// (the rank of the run's first record) at the run's first visibility; the placement pass walks
+// the same runs and gives record j of a run the rank + j, loading that rank and the bucket's
+// offsets once per run. Runs end where the bucket changes (a dropped position ends one) and at
+// the end of a chunk, identically in both passes. Results do not depend on `tracks`: any value
+// bins correctly; it only sets the order of the records within a bucket and the cost.
+constexpr int kTrackChunk = 32;
+
+__device__ __forceinline__ void bucket_keys(const VisPos& vp, int W, int N, int n_strips, int strip_w, int& key1,
+                                            int& key2) {
+  const int strip = strip_of(vp.x0, strip_w);
+  key1 = strip * N + vp.y0;
+  key2 = col_in_strip(vp.x0, strip_w) + W > strip_w ? next_strip(strip, n_strips) * N + vp.y0 : -1;
+}
+
+__global__ void k_bin_count_tracks(const double* __restrict__ uv, long long nvis, long long tracks, double scale2,
+                                   int W, int N, int n_strips, int strip_w, int4* __restrict__ pos,
+                                   int* __restrict__ rank2, int* __restrict__ hist, int* __restrict__ counters,
+                                   double2* __restrict__ frac) {
+  const double2* uv2 = reinterpret_cast<const double2*>(uv);
+  int* pos_w = reinterpret_cast<int*>(pos) + 3;  // the rank field of entry k: pos_w[4 k]
+  const long long n_t = (nvis + tracks - 1) / tracks;
+  const long long n_threads = tracks * ((n_t + kTrackChunk - 1) / kTrackChunk);
+  for (long long g = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; g < n_threads;
+       g += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long b = g % tracks, t0 = (g / tracks) * kTrackChunk;
+    const long long k_end = min(nvis, min(n_t, t0 + kTrackChunk) * tracks);
+    int cur1 = -1, len1 = 0, cur2 = -1, len2 = 0;
+    long long start1 = 0, start2 = 0;
+    // the rank of a run is stored at the next flush, so that the atomic's round trip overlaps
+    // the samples between (a store of its value right away would wait for it)
+    long long pend1 = -1, pend2 = -1;
+    int pval1 = 0, pval2 = 0;
+    for (long long k = t0 * tracks + b; k < k_end; k += tracks) {
+      VisPos vp{0, 0, 0u, 0u};
+      double2 dl = make_double2(0.0, 0.0);
+      const bool ok = vis_position(uv2[k], scale2, W, N, vp, frac != nullptr ? &dl : nullptr);
+      if (frac != nullptr) frac[k] = dl;
+      // rank field: 0 until the run's rank is known (set below for a run's first entry)
+      pos[k] = pack_pos(vp, ok ? 0 : -1);
+      int key1 = -1, key2 = -1;
+      if (ok) bucket_keys(vp, W, N, n_strips, strip_w, key1, key2);
+      else atomicAdd(counters + kCntBad, 1);
+      if (key1 != cur1) {
+        if (len1 > 0) {
+          if (pend1 >= 0) pos_w[4 * pend1] = pval1;
+          pval1 = atomicAdd(hist + cur1, len1);
+          pend1 = start1;
+        }
+        cur1 = key1;
+        start1 = k;
+        len1 = 0;
+      }
+      len1 += key1 >= 0;
+      if (key2 != cur2) {
+        if (len2 > 0) {
+          if (pend2 >= 0) rank2[pend2] = pval2;
+          pval2 = atomicAdd(hist + cur2, len2);
+          pend2 = start2;
+        }
+        cur2 = key2;
+        start2 = k;
+        len2 = 0;
+      }
+      len2 += key2 >= 0;
+    }
+    if (len1 > 0) {
+      if (pend1 >= 0) pos_w[4 * pend1] = pval1;
+      pval1 = atomicAdd(hist + cur1, len1);
+      pend1 = start1;
+    }
+    if (len2 > 0) {
+      if (pend2 >= 0) rank2[pend2] = pval2;
+      pval2 = atomicAdd(hist + cur2, len2);
+      pend2 = start2;
+    }
+    if (pend1 >= 0) pos_w[4 * pend1] = pval1;
+    if (pend2 >= 0) rank2[pend2] = pval2;
+  }
+}
+
+// Placement of the records of one run: the pair's base and the dealt position (see
+// dealt_position) of rank rho = row offset + run rank + j, kept as rho = i nc + jj so that
+// each further record of the run costs no division.
+struct RunPlace {
+  int base, nc, q, r, jj, i;
+  __device__ __forceinline__ void start(const int* __restrict__ offsets, int key, int rank0) {
+    const int g = key & ~1;  // N is even: the pair's first row has an even key
+    const int2 a = *reinterpret_cast<const int2*>(offsets + g);
+    const int n = offsets[g + 2] - a.x;
+    const int rho = ((key & 1) ? a.y - a.x : 0) + rank0;
+    base = a.x;
+    nc = max(1, (n + 31) >> 5);
+    q = n / nc;
+    r = n - q * nc;
+    i = rho / nc;
+    jj = rho - i * nc;
+  }
+  __device__ __forceinline__ int next() {
+    const int pos = base + jj * q + min(jj, r) + i;
+    if (++jj == nc) {
+      jj = 0;
+      ++i;
+    }
+    return pos;
+  }
+};
+
+__global__ void k_bin_scatter_tracks(const int4* __restrict__ pos, const int* __restrict__ rank2, long long nvis,
+                                     long long tracks, int W, int N, int n_strips, int strip_w,
+                                     const int* __restrict__ offsets, Rec* __restrict__ recs) {
+  const long long n_t = (nvis + tracks - 1) / tracks;
+  const long long n_threads = tracks * ((n_t + kTrackChunk - 1) / kTrackChunk);
+  for (long long g = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; g < n_threads;
+       g += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long b = g % tracks, t0 = (g / tracks) * kTrackChunk;
+    const long long k_end = min(nvis, min(n_t, t0 + kTrackChunk) * tracks);
+    int cur1 = -1, cur2 = -1;
+    RunPlace run1{}, run2{};
+    long long k = t0 * tracks + b;
+    int4 c = k < k_end ? __ldcs(pos + k) : make_int4(0, 0, 0, -1);
+    for (; k < k_end; k += tracks) {
+      const int4 cn = k + tracks < k_end ? __ldcs(pos + k + tracks) : make_int4(0, 0, 0, -1);  // one ahead
+      const VisPos vp = unpack_pos(c);
+      int key1 = -1, key2 = -1;
+      if (c.w >= 0) bucket_keys(vp, W, N, n_strips, strip_w, key1, key2);
+      if (key1 != cur1) {
+        cur1 = key1;
+        if (key1 >= 0) run1.start(offsets, key1, c.w);
+      }
+      if (key2 != cur2) {
+        cur2 = key2;
+        if (key2 >= 0) run2.start(offsets, key2, __ldcs(rank2 + k));
+      }
+      if (key1 >= 0) {
+        const int xr = col_in_strip(vp.x0, strip_w);
+        recs[run1.next()] = Rec{static_cast<unsigned>(k), rec_pack(vp.y0, xr), vp.su, vp.sv};
+        if (key2 >= 0) recs[run2.next()] = Rec{static_cast<unsigned>(k), rec_pack(vp.y0, xr - strip_w), vp.su, vp.sv};
+      }
+      c = cn;
     }
   }
 }
@@ -308,14 +490,29 @@ int bin_launch(const BinArgs& a, cudaStream_t st) {
   const int threads = 256;
   const long long want_c = (a.nvis + threads * kCountIlp - 1) / (threads * kCountIlp);
   const int blocks_c = static_cast<int>(want_c < a.max_blocks ? (want_c > 0 ? want_c : 1) : a.max_blocks);
-  k_bin_count<<<blocks_c, threads, 0, st>>>(a.uv, a.nvis, a.scale2, a.W, a.N, a.n_strips, a.strip, a.rank,
-                                          a.hist, a.counters, a.frac);
+  long long n_tthreads = 0;
+  if (a.tracks > 0) {
+    const long long n_t = (a.nvis + a.tracks - 1) / a.tracks;
+    n_tthreads = a.tracks * ((n_t + kTrackChunk - 1) / kTrackChunk);
+  }
+  const long long want_t = (n_tthreads + threads - 1) / threads;
+  const int blocks_t = static_cast<int>(want_t < a.max_blocks ? (want_t > 0 ? want_t : 1) : a.max_blocks);
+  if (a.tracks > 0)
+    k_bin_count_tracks<<<blocks_t, threads, 0, st>>>(a.uv, a.nvis, a.tracks, a.scale2, a.W, a.N, a.n_strips,
+                                                     a.strip, a.pos, a.rank2, a.hist, a.counters, a.frac);
+  else
+    k_bin_count<<<blocks_c, threads, 0, st>>>(a.uv, a.nvis, a.scale2, a.W, a.N, a.n_strips, a.strip, a.pos,
+                                            a.rank2, a.hist, a.counters, a.frac);
   const int nchunks = static_cast<int>((L + kScanChunk - 1) / kScanChunk);
   k_scan_partials<<<nchunks, kScanThreads, 0, st>>>(a.hist, L, a.partial);
   k_scan_top<<<1, 1024, 0, st>>>(a.partial, nchunks);
   k_scan_final<<<nchunks, kScanThreads, 0, st>>>(a.hist, L, a.partial, a.offsets);
-  k_bin_scatter<<<blocks_c, threads, 0, st>>>(a.uv, a.scale2, a.rank, a.nvis, a.W, a.N, a.n_strips, a.strip,
-                                            a.offsets, a.recs);
+  if (a.tracks > 0)
+    k_bin_scatter_tracks<<<blocks_t, threads, 0, st>>>(a.pos, a.rank2, a.nvis, a.tracks, a.W, a.N, a.n_strips,
+                                                       a.strip, a.offsets, a.recs);
+  else
+    k_bin_scatter<<<blocks_c, threads, 0, st>>>(a.pos, a.rank2, a.nvis, a.W, a.N, a.n_strips, a.strip, a.offsets,
+                                              a.recs);
   const int nblk = (a.N + a.rows_per_block - 1) / a.rows_per_block;
   const int ntask = a.n_strips * nblk;
   if (a.rows_per_block > kMaxRowsPerBlock) return -1;

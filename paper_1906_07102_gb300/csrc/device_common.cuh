@@ -19,7 +19,7 @@ struct VisPos {
 // the support-start row (bits 8..31) and xrel (bits 0..7, signed), the support start
 // column relative to the strip's first column (negative when the support started in the
 // previous strip, i.e. for the strip's secondary copy).
-struct Rec {
+struct alignas(16) Rec {  // one 16-byte load or store
   unsigned idx;
   int rx;
   unsigned su, sv;

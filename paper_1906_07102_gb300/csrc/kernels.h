@@ -48,13 +48,18 @@ struct BinArgs {
   int max_blocks;
   int* hist;       // n_strips * N
   int* offsets;    // n_strips * N + 1
-  int2* rank;      // max_vis: rank of the record(s) in their buckets
+  int4* pos;       // max_vis: per visibility (x0 | y0 << 16, su, sv, rank of its record in its
+                   // first bucket; -1 for a dropped position), written by the counting pass
+  int* rank2;      // max_vis: rank of the record in the second bucket (supports crossing a strip)
   int* partial;    // scan chunk sums
   Rec* recs;       // 2 * max_vis
   Item* items;     // item_cap
   int* counters;   // 8
   double2* frac;   // max_vis or NULL: per visibility (u_q - u, v_q - v) in cells, the residual
                    // of the 2^-32 quantisation (float64 plans: exact table fractions)
+  long long tracks;  // > 0: positions ordered k = t * tracks + b (sample t of track b); the
+                     // counting and placement passes then follow each track in runs of
+                     // samples that share a bucket. 0: no order assumed.
 };
 
 int bin_launch(const BinArgs& a, cudaStream_t st);

@@ -74,7 +74,8 @@ struct lmg_plan {
   void* d_h = nullptr;
   int* hist = nullptr;
   int* offsets = nullptr;
-  int2* rank = nullptr;
+  int4* pos = nullptr;
+  int* rank2 = nullptr;
   int* partial = nullptr;
   lmg::Rec* recs = nullptr;
   lmg::Item* items = nullptr;
@@ -104,7 +105,7 @@ struct PlanOptions {
 
 int plan_create(const lmg_table* t, int64_t n_image, double pixel_scale, int64_t max_vis, int dtype,
                 const PlanOptions& opt, lmg_plan** out);
-int plan_bin(lmg_plan* p, const double* uv, int64_t nvis, cudaStream_t st);
+int plan_bin(lmg_plan* p, const double* uv, int64_t nvis, cudaStream_t st, int64_t tracks = 0);
 void free_plan(lmg_plan* p);
 SweepArgs sweep_args(const lmg_plan* p);
 int cuda_error(cudaError_t e, const char* what);

@@ -34,6 +34,7 @@ _SIGS = {
     "lmg_plan_create": (ctypes.c_int, [_vp, _i64, ctypes.c_double, _i64, ctypes.c_int, ctypes.POINTER(_vp)]),
     "lmg_plan_free": (ctypes.c_int, [_vp]),
     "lmg_plan_bin": (ctypes.c_int, [_vp, _vp, _i64, _vp]),
+    "lmg_plan_bin_tracks": (ctypes.c_int, [_vp, _vp, _i64, _i64, _vp]),
     "lmg_plan_dropped": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), _vp]),
     "lmg_plan_info": (ctypes.c_int, [_vp, _vp, _vp]),
     "lmg_work_grid": (_vp, [_vp]),
@@ -172,12 +173,17 @@ class Plan:
         self.W = table.W
         self.nvis = None
 
-    def bin(self, uv):
+    def bin(self, uv, tracks=None):
+        """Bins uv (CUDA float64 [nvis, 2], wavelengths). tracks: number of tracks when the
+        positions are stored sample-major (row k = t * tracks + b), else None."""
         import torch
         uv = _need(uv, torch.float64, None, "uv")
         if uv.dim() != 2 or uv.shape[1] != 2:
             raise ValueError("uv must be [nvis, 2]")
-        _check(lib().lmg_plan_bin(self._h, _ptr(uv), uv.shape[0], _stream()))
+        if tracks is None:
+            _check(lib().lmg_plan_bin(self._h, _ptr(uv), uv.shape[0], _stream()))
+        else:
+            _check(lib().lmg_plan_bin_tracks(self._h, _ptr(uv), uv.shape[0], int(tracks), _stream()))
         self.nvis = uv.shape[0]
         return self
 

@@ -57,6 +57,7 @@ def test_null_outputs_are_rejected(lmg):
     assert L.lmg_kernel_table(7, 0.5, 100, 1, 0, None) == -1
     assert L.lmg_table_export(None, None, 0, None, 0, None, None) == -1
     assert L.lmg_plan_bin(None, None, 0, None) == -1
+    assert L.lmg_plan_bin_tracks(None, None, 0, 1, None) == -1
     assert L.lmg_grid(None, None, None, 0, None, None) == -1
 
 
