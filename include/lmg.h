@@ -23,10 +23,14 @@
  *    exp(-i 2 pi (u l + v m)) (Eq. 2). Weights are real; NULL means all ones.
  *  - dtype LMG_C64: complex64 data, float32 table and float32 arithmetic;
  *    dtype LMG_C128: complex128 data, float64 table and float64 arithmetic.
- *  - Complex arrays are interleaved (re, im) pairs, 8-byte (C64) or 16-byte (C128)
- *    aligned. All data pointers are DEVICE pointers owned by the caller unless a
- *    parameter says "host". The library owns only the opaque table and plan objects
- *    (and the device buffers inside a plan); free them with lmg_*_free.
+ *  - Complex arrays are interleaved (re, im) pairs. Grids ([N][N] arrays that the sweeps
+ *    and transforms read or write) are 16-byte aligned (16-byte vector accesses); images
+ *    and visibility arrays are aligned to their element (8 bytes C64, 16 bytes C128),
+ *    weights to theirs (4 or 8 bytes), uv arrays to 16 bytes. A call given a misaligned
+ *    array returns LMG_EINVAL and does nothing. All data pointers are DEVICE pointers
+ *    owned by the caller unless a parameter says "host". The library owns only the
+ *    opaque table and plan objects (and the device buffers inside a plan); free them
+ *    with lmg_*_free.
  *  - stream is a cudaStream_t passed as void* (NULL = legacy default stream). Every call
  *    that takes a stream only enqueues work and returns without synchronising, except
  *    where a comment says otherwise.
@@ -291,9 +295,9 @@ void* lmg_work_grid(lmg_plan* p);
  * a real-time pipeline that must not allocate while it runs. The paper has no
  * counterpart; this is a deployment variant of the existing path.
  *
- * All working memory (decoded positions and ranks, records, bucket counts, work items,
+ * All working memory (bucket ranks, records, bucket counts, work items,
  * spill rows and the float32 copy of the table) lives in one fixed-size __device__ array
- * of this library, about 21 MB, which every GPU that loads the library holds until the
+ * of this library, about 16 MB, which every GPU that loads the library holds until the
  * process exits.
  * Limits: nvis <= LMG_STATIC_MAX_VIS, grid N = n_image / x0 a multiple of 64 in
  * [64, LMG_STATIC_MAX_N], table oversample <= LMG_STATIC_MAX_OVERSAMPLE; larger sizes

@@ -85,7 +85,7 @@ namespace lmg {
 
 void free_plan(lmg_plan* p) {
   if (!p) return;
-  void* ptrs[] = {p->d_table, p->d_h, p->hist, p->offsets, p->pos, p->rank2, p->partial, p->recs,
+  void* ptrs[] = {p->d_table, p->d_h, p->hist, p->offsets, p->rank, p->partial, p->recs,
                   p->items, p->counters, p->spill, p->frac, p->work, p->model};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -127,6 +127,21 @@ namespace {
 int need_binned(const lmg_plan* p) {
   if (p->nvis < 0) return set_error(LMG_EINVAL, "plan has no binned positions (call lmg_plan_bin first)");
   return LMG_OK;
+}
+
+// Alignment of device arrays: grids (read and written by the sweeps with 16-byte vector
+// accesses) to 16 bytes; images, visibilities and weights to their element size (the
+// correction kernels take two pixels per thread only where both arrays allow it).
+int need_aligned(const void* q, size_t a, const char* what) {
+  if (q && reinterpret_cast<uintptr_t>(q) % a != 0)
+    return set_error(LMG_EINVAL, std::string(what) + " must be " + std::to_string(a) + "-byte aligned");
+  return LMG_OK;
+}
+size_t elem_bytes(int dtype) { return dtype == LMG_C128 ? 16 : 8; }
+int need_vis_aligned(const lmg_plan* p, const void* vis, const void* weights) {
+  const size_t rs = p->dtype == LMG_C128 ? 8 : 4;
+  if (int rc = need_aligned(vis, 2 * rs, "visibilities")) return rc;
+  return need_aligned(weights, rs, "weights");
 }
 
 int launch_status(int rc, const char* what) {
@@ -309,8 +324,7 @@ int plan_create(const lmg_table* t, int64_t n_image, double pixel_scale, int64_t
   if ((rc = dalloc(reinterpret_cast<unsigned char**>(&p->d_table), tab_bytes.size(), "table")) ||
       (rc = dalloc(reinterpret_cast<unsigned char**>(&p->d_h), h_bytes.size(), "correction")) ||
       (rc = dalloc(&p->hist, size_t(L), "histogram")) ||
-      (rc = dalloc(&p->offsets, size_t(L) + 1, "offsets")) || (rc = dalloc(&p->pos, size_t(max_vis), "positions")) ||
-      (rc = dalloc(&p->rank2, size_t(max_vis), "ranks")) ||
+      (rc = dalloc(&p->offsets, size_t(L) + 1, "offsets")) || (rc = dalloc(&p->rank, size_t(max_vis), "ranks")) ||
       (rc = dalloc(&p->partial, size_t(p->nchunks), "scan")) || (rc = dalloc(&p->recs, size_t(2 * max_vis), "records")) ||
       (rc = dalloc(&p->items, size_t(p->item_cap), "items")) || (rc = dalloc(&p->counters, kNumCounters, "counters")) ||
       (rc = dalloc(reinterpret_cast<unsigned char**>(&p->spill), size_t(p->item_cap) * ring_slots(p->W) * strip * c2, "spill")) ||
@@ -408,8 +422,7 @@ int plan_bin(lmg_plan* p, const double* uv, int64_t nvis, cudaStream_t st, int64
   a.max_blocks = p->sms * 8;
   a.hist = p->hist;
   a.offsets = p->offsets;
-  a.pos = p->pos;
-  a.rank2 = p->rank2;
+  a.rank = p->rank;
   a.partial = p->partial;
   a.recs = p->recs;
   a.items = p->items;
@@ -600,6 +613,8 @@ int lmg_grid(lmg_plan* p, const void* vis, const void* weights, int accum, void*
   if (accum != LMG_ACCUM_PLAIN && accum != LMG_ACCUM_COMPENSATED) return set_error(LMG_EINVAL, "bad accum");
   if (accum == LMG_ACCUM_COMPENSATED && p->dtype != LMG_C64)
     return set_error(LMG_EUNSUPPORTED, "compensated accumulation is for LMG_C64");
+  if (int rc = need_aligned(grid, 16, "grid")) return rc;
+  if (int rc = need_vis_aligned(p, vis, weights)) return rc;
   return do_grid(p, vis, weights, accum, grid, static_cast<cudaStream_t>(stream));
 }
 
@@ -608,6 +623,8 @@ int lmg_degrid(lmg_plan* p, const void* grid, void* vis_out, void* stream) {
   if (!p || !grid) return set_error(LMG_EINVAL, "NULL argument");
   if (int rc = need_binned(p)) return rc;
   if (p->nvis > 0 && !vis_out) return set_error(LMG_EINVAL, "vis_out is NULL");
+  if (int rc = need_aligned(grid, 16, "grid")) return rc;
+  if (int rc = need_vis_aligned(p, vis_out, nullptr)) return rc;
   return do_degrid(p, grid, vis_out, static_cast<cudaStream_t>(stream));
 }
 
@@ -615,12 +632,14 @@ int lmg_fft(lmg_plan* p, int direction, void* grid, void* stream) {
   clear_error();
   if (!p || !grid) return set_error(LMG_EINVAL, "NULL argument");
   if (direction != LMG_FFT_IMAGE && direction != LMG_FFT_MODEL) return set_error(LMG_EINVAL, "bad direction");
+  if (int rc = need_aligned(grid, 16, "grid")) return rc;
   return do_fft(p, direction, grid, static_cast<cudaStream_t>(stream));
 }
 
 int lmg_fft_pruned(lmg_plan* p, int direction, void* grid, void* stream) {
   clear_error();
   if (!p || !grid) return set_error(LMG_EINVAL, "NULL argument");
+  if (int rc = need_aligned(grid, 16, "grid")) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (direction == LMG_FFT_IMAGE) return fft_image_pruned(p, grid, st);
   if (direction == LMG_FFT_MODEL) return fft_model_pruned(p, grid, st);
@@ -630,6 +649,8 @@ int lmg_fft_pruned(lmg_plan* p, int direction, void* grid, void* stream) {
 int lmg_grid_correct(lmg_plan* p, int direction, const void* in, void* out, void* stream) {
   clear_error();
   if (!p || !in || !out) return set_error(LMG_EINVAL, "NULL argument");
+  if (int rc = need_aligned(in, elem_bytes(p->dtype), "in")) return rc;
+  if (int rc = need_aligned(out, elem_bytes(p->dtype), "out")) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int rc;
   if (direction == LMG_CROP) rc = crop_correct_launch(in, out, p->d_h, int(p->n_image), int(p->N), p->dtype, st);
@@ -647,6 +668,8 @@ int lmg_dirty_image(lmg_plan* p, const void* vis, const void* weights, int accum
   if (accum != LMG_ACCUM_PLAIN && accum != LMG_ACCUM_COMPENSATED) return set_error(LMG_EINVAL, "bad accum");
   if (accum == LMG_ACCUM_COMPENSATED && p->dtype != LMG_C64)
     return set_error(LMG_EUNSUPPORTED, "compensated accumulation is for LMG_C64");
+  if (int rc = need_aligned(image_out, elem_bytes(p->dtype), "image")) return rc;
+  if (int rc = need_vis_aligned(p, vis, weights)) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int rc = do_grid(p, vis, weights, accum, p->work, st);
   if (rc == LMG_OK) rc = fft_image_pruned(p, p->work, st);
@@ -662,6 +685,8 @@ int lmg_predict_vis(lmg_plan* p, const void* image, void* vis_out, void* stream)
   if (int rc = need_binned(p)) return rc;
   if (!p->work) return set_error(LMG_EINVAL, "plan has no work grids (LMG_PLAN_NO_WORK_GRIDS): use lmg_predict_vis_ws");
   if (p->nvis > 0 && !vis_out) return set_error(LMG_EINVAL, "vis_out is NULL");
+  if (int rc = need_aligned(image, elem_bytes(p->dtype), "image")) return rc;
+  if (int rc = need_vis_aligned(p, vis_out, nullptr)) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int rc = launch_status(pad_rows_launch(image, p->model, p->d_h, int(p->n_image), int(p->N), p->dtype, st), "pad");
   if (rc == LMG_OK) rc = fft_model_to_work(p, st);
@@ -705,6 +730,8 @@ int lmg_dirty_image_ws(lmg_plan* p, const void* vis, const void* weights, int ac
   if (accum != LMG_ACCUM_PLAIN && accum != LMG_ACCUM_COMPENSATED) return set_error(LMG_EINVAL, "bad accum");
   if (accum == LMG_ACCUM_COMPENSATED && p->dtype != LMG_C64)
     return set_error(LMG_EUNSUPPORTED, "compensated accumulation is for LMG_C64");
+  if (int rc = need_aligned(image_out, elem_bytes(p->dtype), "image")) return rc;
+  if (int rc = need_vis_aligned(p, vis, weights)) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int rc = do_grid(p, vis, weights, accum, workspace, st);
   if (rc == LMG_OK) rc = fft_image_pruned(p, workspace, st);
@@ -720,6 +747,8 @@ int lmg_predict_vis_ws(lmg_plan* p, const void* image, void* vis_out, void* work
   if (int rc = need_binned(p)) return rc;
   if (int rc = check_workspace(p, workspace, ws_bytes)) return rc;
   if (p->nvis > 0 && !vis_out) return set_error(LMG_EINVAL, "vis_out is NULL");
+  if (int rc = need_aligned(image, elem_bytes(p->dtype), "image")) return rc;
+  if (int rc = need_vis_aligned(p, vis_out, nullptr)) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // the whole workspace is written (zero outside the kept pixels), then transformed in place
   int rc = launch_status(pad_correct_launch(image, workspace, p->d_h, int(p->n_image), int(p->N), p->dtype, st), "pad");
@@ -735,6 +764,9 @@ int lmg_correct_factors(int direction, const void* in, void* out, const void* h,
   if (n_image < 2 || (n_image & 1) || N < n_image || (N & 1) || N > 65536)
     return set_error(LMG_EINVAL, "need even n_image >= 2 and even N in [n_image, 65536]");
   if (dtype != LMG_C64 && dtype != LMG_C128) return set_error(LMG_EINVAL, "dtype must be LMG_C64 or LMG_C128");
+  if (int rc = need_aligned(in, elem_bytes(dtype), "in")) return rc;
+  if (int rc = need_aligned(out, elem_bytes(dtype), "out")) return rc;
+  if (int rc = need_aligned(h, dtype == LMG_C128 ? 8 : 4, "h")) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int rc;
   if (direction == LMG_CROP) rc = crop_correct_launch(in, out, h, int(n_image), int(N), dtype, st);

@@ -496,12 +496,26 @@ std::vector<uintptr_t> make_key(int op, int n, std::initializer_list<const void*
   return key;
 }
 
-int check_ptrs(const lmg_batch* b, const void* const* arr, const char* what, bool need_nonnull_entries) {
+// Pointer arrays of a batch call: non-NULL where needed, and aligned (visibilities and
+// weights to their element, grids and images to 16 bytes: the kernels use vector accesses).
+int check_ptrs(const lmg_batch* b, const void* const* arr, const char* what, bool need_nonnull_entries,
+               size_t align = 8) {
   if (!arr) return set_error(LMG_EINVAL, std::string("batch: ") + what + " is NULL");
-  for (int c = 0; c < b->n_chan; ++c)
+  for (int c = 0; c < b->n_chan; ++c) {
     if (need_nonnull_entries && !arr[c] && b->plans[size_t(c)]->nvis > 0)
       return set_error(LMG_EINVAL, std::string("batch: ") + what + "[" + std::to_string(c) + "] is NULL");
+    if (arr[c] && reinterpret_cast<uintptr_t>(arr[c]) % align != 0)
+      return set_error(LMG_EINVAL, std::string("batch: ") + what + "[" + std::to_string(c) + "] must be " +
+                                       std::to_string(align) + "-byte aligned");
+  }
   return LMG_OK;
+}
+
+int check_arrays(const lmg_batch* b, const void* const* arr, const char* what) {
+  if (!arr) return set_error(LMG_EINVAL, std::string("batch: ") + what + " is NULL");
+  for (int c = 0; c < b->n_chan; ++c)
+    if (!arr[c]) return set_error(LMG_EINVAL, std::string("batch: ") + what + "[" + std::to_string(c) + "] is NULL");
+  return check_ptrs(b, arr, what, true, 16);
 }
 
 int need_binned(const lmg_batch* b) {
@@ -686,9 +700,9 @@ int lmg_batch_grid(lmg_batch* b, const void* const* vis, const void* const* weig
   if (!b) return set_error(LMG_EINVAL, "batch is NULL");
   if (int rc = need_binned(b)) return rc;
   if (int rc = check_ptrs(b, vis, "vis", true)) return rc;
-  if (!grid) return set_error(LMG_EINVAL, "batch: grid is NULL");
-  for (int c = 0; c < b->n_chan; ++c)
-    if (!grid[c]) return set_error(LMG_EINVAL, "batch: grid[" + std::to_string(c) + "] is NULL");
+  if (weights)
+    if (int rc = check_ptrs(b, weights, "weights", false, 4)) return rc;
+  if (int rc = check_arrays(b, const_cast<const void* const*>(grid), "grid")) return rc;
   const auto key = make_key(kOpGrid, b->n_chan, {vis, weights, const_cast<const void* const*>(grid)});
   return run_graph(
       b, kOpGrid, key, static_cast<cudaStream_t>(stream), [&] { return fill_sweeps(b, kOpGrid, vis, weights, grid); },
@@ -699,9 +713,7 @@ int lmg_batch_degrid(lmg_batch* b, const void* const* grid, void* const* vis_out
   clear_error();
   if (!b) return set_error(LMG_EINVAL, "batch is NULL");
   if (int rc = need_binned(b)) return rc;
-  if (!grid) return set_error(LMG_EINVAL, "batch: grid is NULL");
-  for (int c = 0; c < b->n_chan; ++c)
-    if (!grid[c]) return set_error(LMG_EINVAL, "batch: grid[" + std::to_string(c) + "] is NULL");
+  if (int rc = check_arrays(b, grid, "grid")) return rc;
   if (int rc = check_ptrs(b, const_cast<const void* const*>(vis_out), "vis_out", true)) return rc;
   const auto key = make_key(kOpDegrid, b->n_chan, {grid, const_cast<const void* const*>(vis_out)});
   return run_graph(
@@ -716,9 +728,9 @@ int lmg_batch_dirty_image(lmg_batch* b, const void* const* vis, const void* cons
   if (!b) return set_error(LMG_EINVAL, "batch is NULL");
   if (int rc = need_binned(b)) return rc;
   if (int rc = check_ptrs(b, vis, "vis", true)) return rc;
-  if (!image) return set_error(LMG_EINVAL, "batch: image is NULL");
-  for (int c = 0; c < b->n_chan; ++c)
-    if (!image[c]) return set_error(LMG_EINVAL, "batch: image[" + std::to_string(c) + "] is NULL");
+  if (weights)
+    if (int rc = check_ptrs(b, weights, "weights", false, 4)) return rc;
+  if (int rc = check_arrays(b, const_cast<const void* const*>(image), "image")) return rc;
   const auto key = make_key(kOpDirty, b->n_chan, {vis, weights, const_cast<const void* const*>(image)});
   return run_graph(
       b, kOpDirty, key, static_cast<cudaStream_t>(stream),
@@ -742,9 +754,7 @@ int lmg_batch_predict_vis(lmg_batch* b, const void* const* image, void* const* v
   clear_error();
   if (!b) return set_error(LMG_EINVAL, "batch is NULL");
   if (int rc = need_binned(b)) return rc;
-  if (!image) return set_error(LMG_EINVAL, "batch: image is NULL");
-  for (int c = 0; c < b->n_chan; ++c)
-    if (!image[c]) return set_error(LMG_EINVAL, "batch: image[" + std::to_string(c) + "] is NULL");
+  if (int rc = check_arrays(b, image, "image")) return rc;
   if (int rc = check_ptrs(b, const_cast<const void* const*>(vis_out), "vis_out", true)) return rc;
   const auto key = make_key(kOpPredict, b->n_chan, {image, const_cast<const void* const*>(vis_out)});
   return run_graph(

@@ -5,12 +5,11 @@
 // Pipeline (all on one stream, no host synchronisation):
 //   1. k_bin_count   per visibility: float64 product to cells, exact fixed-point support
 //                    rule, strip keys (one, or two when the support crosses into the next
-//                    strip); the bucket counter's returned value is the record's rank. The
-//                    decoded position (cell, table coordinates, rank) is stored in one
-//                    16-byte entry per visibility, so that the next pass does no float64 or
-//                    fixed-point work (float64 runs at a small fraction of the float32 rate).
+//                    strip); the bucket counter's returned value is the record's rank.
 //   2. scan          exclusive prefix sum of the bucket counts (strip-major, row-minor).
-//   3. k_bin_scatter records of each pair of rows (2m, 2m+1) of a strip -- the row group
+//   3. k_bin_scatter positions recomputed from (u, v) (measured cheaper than storing a
+//                    decoded 16-byte position per visibility and reloading it), records
+//                    of each pair of rows (2m, 2m+1) of a strip -- the row group
 //                    the sweeps stage together -- to the pair's range, dealt so that any 32
 //                    consecutive records sample the whole pair (see dealt_position).
 //   4. k_make_items  per strip and block of rows: items holding about item_target records,
@@ -53,17 +52,6 @@ __device__ __forceinline__ int strip_of(int x0, int strip_w) { return x0 >> (__f
 __device__ __forceinline__ int col_in_strip(int x0, int strip_w) { return x0 & (strip_w - 1); }
 __device__ __forceinline__ int next_strip(int strip, int n_strips) { return strip + 1 == n_strips ? 0 : strip + 1; }
 
-// The 16-byte position entry (N <= 65536: the cell indices take 16 bits each); w carries a
-// rank (>= 0) or -1 for a dropped position.
-__device__ __forceinline__ int4 pack_pos(const VisPos& vp, int w) {
-  const unsigned xy = static_cast<unsigned>(vp.x0) | (static_cast<unsigned>(vp.y0) << 16);
-  return make_int4(static_cast<int>(xy), static_cast<int>(vp.su), static_cast<int>(vp.sv), w);
-}
-__device__ __forceinline__ VisPos unpack_pos(int4 c) {
-  return VisPos{c.x & 0xffff, static_cast<int>(static_cast<unsigned>(c.x) >> 16), static_cast<unsigned>(c.y),
-                static_cast<unsigned>(c.z)};
-}
-
 // Pass 1: positions to grid cells (support rule), bucket keys, and each record's rank in
 // its bucket (the value returned by the bucket counter), so that pass 2 needs no atomics.
 // Each thread takes kCountIlp positions per iteration so that their bucket atomics are in
@@ -71,8 +59,8 @@ __device__ __forceinline__ VisPos unpack_pos(int4 c) {
 constexpr int kCountIlp = 4;
 
 __global__ void k_bin_count(const double* __restrict__ uv, long long nvis, double scale2, int W,
-                            int N, int n_strips, int strip_w, int4* __restrict__ pos, int* __restrict__ rank2,
-                            int* __restrict__ hist, int* __restrict__ counters, double2* __restrict__ frac) {
+                            int N, int n_strips, int strip_w, int2* __restrict__ rank, int* __restrict__ hist,
+                            int* __restrict__ counters, double2* __restrict__ frac) {
   const int lane = threadIdx.x & 31;  // for the dropped-position count
   const long long span = static_cast<long long>(blockDim.x) * kCountIlp;
   const long long stride = static_cast<long long>(gridDim.x) * span;
@@ -85,7 +73,7 @@ __global__ void k_bin_count(const double* __restrict__ uv, long long nvis, doubl
       const long long k = base + u * blockDim.x + threadIdx.x;
       key1[u] = key2[u] = -1;
       bad[u] = false;
-      vp[u] = VisPos{0, 0, 0u, 0u};
+      vp[u] = VisPos{-1, 0, 0u, 0u};
       if (k < nvis) {
         double2 dl = make_double2(0.0, 0.0);
         const bool ok = vis_position(reinterpret_cast<const double2*>(uv)[k], scale2, W, N, vp[u],
@@ -103,16 +91,13 @@ __global__ void k_bin_count(const double* __restrict__ uv, long long nvis, doubl
     int2 rk[kCountIlp];
 #pragma unroll
     for (int u = 0; u < kCountIlp; ++u) {
-      rk[u].x = key1[u] >= 0 ? atomicAdd(hist + key1[u], 1) : -1;
+      rk[u].x = key1[u] >= 0 ? atomicAdd(hist + key1[u], 1) : 0;
       rk[u].y = key2[u] >= 0 ? atomicAdd(hist + key2[u], 1) : 0;
     }
 #pragma unroll
     for (int u = 0; u < kCountIlp; ++u) {
       const long long k = base + u * blockDim.x + threadIdx.x;
-      if (k < nvis) {
-        pos[k] = pack_pos(vp[u], rk[u].x);
-        rank2[k] = rk[u].y;
-      }
+      if (k < nvis) rank[k] = rk[u];
       const unsigned nb = __popc(__ballot_sync(0xffffffffu, bad[u]));
       if (lane == 0 && nb) atomicAdd(counters + kCntBad, static_cast<int>(nb));
     }
@@ -221,42 +206,37 @@ __device__ __forceinline__ int dealt_position(int rho, int n) {
   return j * q + min(j, r) + rho / nc;
 }
 
-__global__ void k_bin_scatter(const int4* __restrict__ pos, const int* __restrict__ rank2, long long nvis, int W,
-                              int N, int n_strips, int strip_w, const int* __restrict__ offsets,
-                              Rec* __restrict__ recs) {
-  // kCountIlp visibilities per thread per iteration: their position and offset loads are in
-  // flight together (the pass is bound by its random L2 requests and their latency). The
-  // positions and ranks are read for the last time here: streaming loads (evict first)
+__global__ void k_bin_scatter(const double* __restrict__ uv, double scale2, const int2* __restrict__ rank,
+                              long long nvis, int W, int N, int n_strips, int strip_w,
+                              const int* __restrict__ offsets, Rec* __restrict__ recs) {
+  // kCountIlp visibilities per thread per iteration: their position, rank and offset loads
+  // are in flight together (the pass is bound by its random L2 requests and their latency).
+  // (u, v) and the ranks are read for the last time here: streaming loads (evict first)
   // leave the L2 to the offsets and the records being written.
   const long long span = static_cast<long long>(blockDim.x) * kCountIlp;
   const long long stride = static_cast<long long>(gridDim.x) * span;
   for (long long base = static_cast<long long>(blockIdx.x) * span; base < nvis; base += stride) {
     VisPos vp[kCountIlp];
-    int r1[kCountIlp];
+    int2 rk[kCountIlp];
 #pragma unroll
     for (int u = 0; u < kCountIlp; ++u) {
       const long long k = base + u * blockDim.x + threadIdx.x;
-      r1[u] = -1;
-      vp[u] = VisPos{0, 0, 0u, 0u};
+      vp[u] = VisPos{-1, 0, 0u, 0u};
+      rk[u] = make_int2(0, 0);
       if (k < nvis) {
-        const int4 c = __ldcs(pos + k);
-        vp[u] = unpack_pos(c);
-        r1[u] = c.w;
+        rk[u] = __ldcs(rank + k);
+        vis_position(__ldcs(reinterpret_cast<const double2*>(uv) + k), scale2, W, N, vp[u]);
       }
     }
-    int g1[kCountIlp], g2[kCountIlp], r2[kCountIlp];  // bucket pair bases (-1: none)
+    int g1[kCountIlp], g2[kCountIlp];  // bucket pair bases (-1: none)
 #pragma unroll
     for (int u = 0; u < kCountIlp; ++u) {
       g1[u] = g2[u] = -1;
-      r2[u] = 0;
-      if (r1[u] >= 0) {
+      if (vp[u].x0 >= 0) {
         const int strip = strip_of(vp[u].x0, strip_w), xr = col_in_strip(vp[u].x0, strip_w);
         const int pair_row = vp[u].y0 & ~1;
         g1[u] = strip * N + pair_row;
-        if (xr + W > strip_w) {
-          g2[u] = next_strip(strip, n_strips) * N + pair_row;
-          r2[u] = __ldcs(rank2 + base + u * blockDim.x + threadIdx.x);
-        }
+        if (xr + W > strip_w) g2[u] = next_strip(strip, n_strips) * N + pair_row;
       }
     }
     // offsets of the pair's two rows and of the next pair (g is even: one 8-byte load and one
@@ -279,10 +259,10 @@ __global__ void k_bin_scatter(const int4* __restrict__ pos, const int* __restric
       const long long k = base + u * blockDim.x + threadIdx.x;
       const int odd = vp[u].y0 & 1, xr = col_in_strip(vp[u].x0, strip_w);
       // row pair (y0 & ~1, y0 | 1) of the strip: [offsets[g], offsets[g + 2])
-      recs[o1[u][0] + dealt_position((odd ? o1[u][1] - o1[u][0] : 0) + r1[u], o1[u][2] - o1[u][0])] =
+      recs[o1[u][0] + dealt_position((odd ? o1[u][1] - o1[u][0] : 0) + rk[u].x, o1[u][2] - o1[u][0])] =
           Rec{static_cast<unsigned>(k), rec_pack(vp[u].y0, xr), vp[u].su, vp[u].sv};
       if (g2[u] >= 0)
-        recs[o2[u][0] + dealt_position((odd ? o2[u][1] - o2[u][0] : 0) + r2[u], o2[u][2] - o2[u][0])] =
+        recs[o2[u][0] + dealt_position((odd ? o2[u][1] - o2[u][0] : 0) + rk[u].y, o2[u][2] - o2[u][0])] =
             Rec{static_cast<unsigned>(k), rec_pack(vp[u].y0, xr - strip_w), vp[u].su, vp[u].sv};
     }
   }
@@ -310,11 +290,10 @@ __device__ __forceinline__ void bucket_keys(const VisPos& vp, int W, int N, int 
 }
 
 __global__ void k_bin_count_tracks(const double* __restrict__ uv, long long nvis, long long tracks, double scale2,
-                                   int W, int N, int n_strips, int strip_w, int4* __restrict__ pos,
-                                   int* __restrict__ rank2, int* __restrict__ hist, int* __restrict__ counters,
-                                   double2* __restrict__ frac) {
+                                   int W, int N, int n_strips, int strip_w, int2* __restrict__ rank,
+                                   int* __restrict__ hist, int* __restrict__ counters, double2* __restrict__ frac) {
   const double2* uv2 = reinterpret_cast<const double2*>(uv);
-  int* pos_w = reinterpret_cast<int*>(pos) + 3;  // the rank field of entry k: pos_w[4 k]
+  int* rank1 = reinterpret_cast<int*>(rank);  // rank[k].x = rank1[2 k], rank[k].y = rank1[2 k + 1]
   const long long n_t = (nvis + tracks - 1) / tracks;
   const long long n_threads = tracks * ((n_t + kTrackChunk - 1) / kTrackChunk);
   for (long long g = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; g < n_threads;
@@ -332,14 +311,12 @@ __global__ void k_bin_count_tracks(const double* __restrict__ uv, long long nvis
       double2 dl = make_double2(0.0, 0.0);
       const bool ok = vis_position(uv2[k], scale2, W, N, vp, frac != nullptr ? &dl : nullptr);
       if (frac != nullptr) frac[k] = dl;
-      // rank field: 0 until the run's rank is known (set below for a run's first entry)
-      pos[k] = pack_pos(vp, ok ? 0 : -1);
       int key1 = -1, key2 = -1;
       if (ok) bucket_keys(vp, W, N, n_strips, strip_w, key1, key2);
       else atomicAdd(counters + kCntBad, 1);
       if (key1 != cur1) {
         if (len1 > 0) {
-          if (pend1 >= 0) pos_w[4 * pend1] = pval1;
+          if (pend1 >= 0) rank1[2 * pend1] = pval1;
           pval1 = atomicAdd(hist + cur1, len1);
           pend1 = start1;
         }
@@ -350,7 +327,7 @@ __global__ void k_bin_count_tracks(const double* __restrict__ uv, long long nvis
       len1 += key1 >= 0;
       if (key2 != cur2) {
         if (len2 > 0) {
-          if (pend2 >= 0) rank2[pend2] = pval2;
+          if (pend2 >= 0) rank1[2 * pend2 + 1] = pval2;
           pval2 = atomicAdd(hist + cur2, len2);
           pend2 = start2;
         }
@@ -361,17 +338,17 @@ __global__ void k_bin_count_tracks(const double* __restrict__ uv, long long nvis
       len2 += key2 >= 0;
     }
     if (len1 > 0) {
-      if (pend1 >= 0) pos_w[4 * pend1] = pval1;
+      if (pend1 >= 0) rank1[2 * pend1] = pval1;
       pval1 = atomicAdd(hist + cur1, len1);
       pend1 = start1;
     }
     if (len2 > 0) {
-      if (pend2 >= 0) rank2[pend2] = pval2;
+      if (pend2 >= 0) rank1[2 * pend2 + 1] = pval2;
       pval2 = atomicAdd(hist + cur2, len2);
       pend2 = start2;
     }
-    if (pend1 >= 0) pos_w[4 * pend1] = pval1;
-    if (pend2 >= 0) rank2[pend2] = pval2;
+    if (pend1 >= 0) rank1[2 * pend1] = pval1;
+    if (pend2 >= 0) rank1[2 * pend2 + 1] = pval2;
   }
 }
 
@@ -402,9 +379,11 @@ struct RunPlace {
   }
 };
 
-__global__ void k_bin_scatter_tracks(const int4* __restrict__ pos, const int* __restrict__ rank2, long long nvis,
-                                     long long tracks, int W, int N, int n_strips, int strip_w,
+__global__ void k_bin_scatter_tracks(const double* __restrict__ uv, double scale2, const int2* __restrict__ rank,
+                                     long long nvis, long long tracks, int W, int N, int n_strips, int strip_w,
                                      const int* __restrict__ offsets, Rec* __restrict__ recs) {
+  const double2* uv2 = reinterpret_cast<const double2*>(uv);
+  const int* rank1 = reinterpret_cast<const int*>(rank);
   const long long n_t = (nvis + tracks - 1) / tracks;
   const long long n_threads = tracks * ((n_t + kTrackChunk - 1) / kTrackChunk);
   for (long long g = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; g < n_threads;
@@ -413,27 +392,23 @@ __global__ void k_bin_scatter_tracks(const int4* __restrict__ pos, const int* __
     const long long k_end = min(nvis, min(n_t, t0 + kTrackChunk) * tracks);
     int cur1 = -1, cur2 = -1;
     RunPlace run1{}, run2{};
-    long long k = t0 * tracks + b;
-    int4 c = k < k_end ? __ldcs(pos + k) : make_int4(0, 0, 0, -1);
-    for (; k < k_end; k += tracks) {
-      const int4 cn = k + tracks < k_end ? __ldcs(pos + k + tracks) : make_int4(0, 0, 0, -1);  // one ahead
-      const VisPos vp = unpack_pos(c);
+    for (long long k = t0 * tracks + b; k < k_end; k += tracks) {
+      VisPos vp;
+      const bool ok = vis_position(__ldcs(uv2 + k), scale2, W, N, vp);
       int key1 = -1, key2 = -1;
-      if (c.w >= 0) bucket_keys(vp, W, N, n_strips, strip_w, key1, key2);
+      if (ok) bucket_keys(vp, W, N, n_strips, strip_w, key1, key2);
       if (key1 != cur1) {
         cur1 = key1;
-        if (key1 >= 0) run1.start(offsets, key1, c.w);
+        if (key1 >= 0) run1.start(offsets, key1, __ldcs(rank1 + 2 * k));
       }
       if (key2 != cur2) {
         cur2 = key2;
-        if (key2 >= 0) run2.start(offsets, key2, __ldcs(rank2 + k));
+        if (key2 >= 0) run2.start(offsets, key2, __ldcs(rank1 + 2 * k + 1));
       }
-      if (key1 >= 0) {
-        const int xr = col_in_strip(vp.x0, strip_w);
-        recs[run1.next()] = Rec{static_cast<unsigned>(k), rec_pack(vp.y0, xr), vp.su, vp.sv};
-        if (key2 >= 0) recs[run2.next()] = Rec{static_cast<unsigned>(k), rec_pack(vp.y0, xr - strip_w), vp.su, vp.sv};
-      }
-      c = cn;
+      if (key1 < 0) continue;
+      const int xr = col_in_strip(vp.x0, strip_w);
+      recs[run1.next()] = Rec{static_cast<unsigned>(k), rec_pack(vp.y0, xr), vp.su, vp.sv};
+      if (key2 >= 0) recs[run2.next()] = Rec{static_cast<unsigned>(k), rec_pack(vp.y0, xr - strip_w), vp.su, vp.sv};
     }
   }
 }
@@ -499,20 +474,20 @@ int bin_launch(const BinArgs& a, cudaStream_t st) {
   const int blocks_t = static_cast<int>(want_t < a.max_blocks ? (want_t > 0 ? want_t : 1) : a.max_blocks);
   if (a.tracks > 0)
     k_bin_count_tracks<<<blocks_t, threads, 0, st>>>(a.uv, a.nvis, a.tracks, a.scale2, a.W, a.N, a.n_strips,
-                                                     a.strip, a.pos, a.rank2, a.hist, a.counters, a.frac);
+                                                     a.strip, a.rank, a.hist, a.counters, a.frac);
   else
-    k_bin_count<<<blocks_c, threads, 0, st>>>(a.uv, a.nvis, a.scale2, a.W, a.N, a.n_strips, a.strip, a.pos,
-                                            a.rank2, a.hist, a.counters, a.frac);
+    k_bin_count<<<blocks_c, threads, 0, st>>>(a.uv, a.nvis, a.scale2, a.W, a.N, a.n_strips, a.strip, a.rank,
+                                            a.hist, a.counters, a.frac);
   const int nchunks = static_cast<int>((L + kScanChunk - 1) / kScanChunk);
   k_scan_partials<<<nchunks, kScanThreads, 0, st>>>(a.hist, L, a.partial);
   k_scan_top<<<1, 1024, 0, st>>>(a.partial, nchunks);
   k_scan_final<<<nchunks, kScanThreads, 0, st>>>(a.hist, L, a.partial, a.offsets);
   if (a.tracks > 0)
-    k_bin_scatter_tracks<<<blocks_t, threads, 0, st>>>(a.pos, a.rank2, a.nvis, a.tracks, a.W, a.N, a.n_strips,
-                                                       a.strip, a.offsets, a.recs);
+    k_bin_scatter_tracks<<<blocks_t, threads, 0, st>>>(a.uv, a.scale2, a.rank, a.nvis, a.tracks, a.W, a.N,
+                                                       a.n_strips, a.strip, a.offsets, a.recs);
   else
-    k_bin_scatter<<<blocks_c, threads, 0, st>>>(a.pos, a.rank2, a.nvis, a.W, a.N, a.n_strips, a.strip, a.offsets,
-                                              a.recs);
+    k_bin_scatter<<<blocks_c, threads, 0, st>>>(a.uv, a.scale2, a.rank, a.nvis, a.W, a.N, a.n_strips, a.strip,
+                                              a.offsets, a.recs);
   const int nblk = (a.N + a.rows_per_block - 1) / a.rows_per_block;
   const int ntask = a.n_strips * nblk;
   if (a.rows_per_block > kMaxRowsPerBlock) return -1;

@@ -48,9 +48,7 @@ struct BinArgs {
   int max_blocks;
   int* hist;       // n_strips * N
   int* offsets;    // n_strips * N + 1
-  int4* pos;       // max_vis: per visibility (x0 | y0 << 16, su, sv, rank of its record in its
-                   // first bucket; -1 for a dropped position), written by the counting pass
-  int* rank2;      // max_vis: rank of the record in the second bucket (supports crossing a strip)
+  int2* rank;      // max_vis: rank of the record(s) in their buckets
   int* partial;    // scan chunk sums
   Rec* recs;       // 2 * max_vis
   Item* items;     // item_cap

@@ -74,8 +74,7 @@ struct lmg_plan {
   void* d_h = nullptr;
   int* hist = nullptr;
   int* offsets = nullptr;
-  int4* pos = nullptr;
-  int* rank2 = nullptr;
+  int2* rank = nullptr;
   int* partial = nullptr;
   lmg::Rec* recs = nullptr;
   lmg::Item* items = nullptr;

@@ -38,9 +38,8 @@ constexpr size_t up256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // Byte offsets of the buffers inside the scratch array (sized for the maxima above).
 constexpr size_t kOffTable = 0;
-constexpr size_t kOffPos = kOffTable + up256(sizeof(float) * (kMaxOversample + 1) * kMaxWp);
-constexpr size_t kOffRank2 = kOffPos + up256(sizeof(int4) * kMaxVis);
-constexpr size_t kOffHist = kOffRank2 + up256(sizeof(int) * kMaxVis);
+constexpr size_t kOffRank = kOffTable + up256(sizeof(float) * (kMaxOversample + 1) * kMaxWp);
+constexpr size_t kOffHist = kOffRank + up256(sizeof(int2) * kMaxVis);
 constexpr size_t kOffOffsets = kOffHist + up256(sizeof(int) * kMaxBuckets);
 constexpr size_t kOffPartial = kOffOffsets + up256(sizeof(int) * (kMaxBuckets + 1));
 constexpr size_t kOffRecs = kOffPartial + up256(sizeof(int) * (kMaxBuckets / 4096 + 2));
@@ -185,8 +184,7 @@ extern "C" int lmg_grid_static(const lmg_table* t, int64_t n_image, double pixel
   b.item_target = kItemTarget;
   b.item_cap = item_cap;
   b.max_blocks = s->sms * 8;
-  b.pos = reinterpret_cast<int4*>(base + kOffPos);
-  b.rank2 = reinterpret_cast<int*>(base + kOffRank2);
+  b.rank = reinterpret_cast<int2*>(base + kOffRank);
   b.hist = reinterpret_cast<int*>(base + kOffHist);
   b.offsets = reinterpret_cast<int*>(base + kOffOffsets);
   b.partial = reinterpret_cast<int*>(base + kOffPartial);

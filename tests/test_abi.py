@@ -224,3 +224,19 @@ def test_new_entry_point_argument_errors(lmg):
     assert L.lmg_correct_factors(0, p16, p16, p16, 64, 128, 2, None) == -1
     assert L.lmg_correct_factors(2, p16, p16, p16, 64, 128, 0, None) == -1
     assert "direction" in L.lmg_last_error().decode()
+
+
+def test_misaligned_arrays_are_rejected_before_device_work(lmg):
+    """Device arrays are checked for alignment before anything is launched: a grid or image
+    view that is not 16-byte aligned, or a visibility array off its element size, is
+    LMG_EINVAL (NULL plan and pointer arguments are checked first, so no device is needed)."""
+    L = lmg.lib()
+    p4 = ctypes.c_void_p(256 + 4)
+    p8 = ctypes.c_void_p(256 + 8)
+    p16 = ctypes.c_void_p(256)
+    assert L.lmg_correct_factors(0, p4, p16, p16, 64, 128, 0, None) == -1
+    assert "in must be 8-byte aligned" in L.lmg_last_error().decode()
+    assert L.lmg_correct_factors(0, p16, p8, p16, 64, 128, 1, None) == -1
+    assert "out must be 16-byte aligned" in L.lmg_last_error().decode()
+    assert L.lmg_correct_factors(0, p16, p16, ctypes.c_void_p(258), 64, 128, 0, None) == -1
+    assert "h must be 4-byte aligned" in L.lmg_last_error().decode()

@@ -117,3 +117,30 @@ def test_fp32_fma_rate_is_plausible():
     r = lmg.fp32_fma_rate()
     # 152 SMs x 128 lanes x 2 flop x ~2 GHz is about 78 TFLOP/s
     assert 2e13 < r < 2e14
+
+
+
+def test_misaligned_views_are_rejected(case):
+    """A grid or visibility view off its alignment is LMG_EINVAL before any launch (the
+    kernels read and write grids with 16-byte vector accesses)."""
+    t, dl, uvd, visd, model = case
+    p = lmg.Plan(t, n_img, dl, uvd.shape[0])
+    p.bin(uvd)
+    buf = torch.zeros(N * N + 1, dtype=torch.complex64, device="cuda")
+    g_off = buf[1:].view(N, N)                 # 8 bytes past a 16-byte boundary
+    with pytest.raises(lmg.LmgError, match="grid must be 16-byte aligned"):
+        p.grid(visd, out=g_off)
+    with pytest.raises(lmg.LmgError, match="grid must be 16-byte aligned"):
+        p.degrid(g_off)
+    # a visibility array 4 bytes past an 8-byte boundary (torch makes no such complex view:
+    # the pointer goes to the C call directly)
+    import ctypes
+    vb = torch.zeros(2 * visd.shape[0] + 2, dtype=torch.float32, device="cuda")
+    g = p.grid(visd)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    L = lmg.lib()
+    assert L.lmg_degrid(p._h, ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(vb.data_ptr() + 4), stream) == -1
+    assert "visibilities must be 8-byte aligned" in L.lmg_last_error().decode()
+    # the plan still works after the refusals
+    g = p.grid(visd)
+    assert torch.isfinite(torch.view_as_real(g)).all()
