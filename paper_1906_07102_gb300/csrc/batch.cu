@@ -256,12 +256,17 @@ struct WClass {
   int blocks[2] = {0, 0};
 };
 
-// Channels sharing one grid size: contiguous work grids and one batched FFT plan.
+// Channels sharing one grid size: contiguous work grids and the 1-D cuFFT plans of the
+// pruned transforms (only the kept field of the image is needed, Eq. 4): every row and
+// the kept columns for imaging, the kept rows and every column for prediction. h is half
+// the largest kept width of the class's channels (a channel with a narrower field has
+// zero rows there, or unused columns, so a wider pruning is still exact).
 struct SizeClass {
   int64_t N = 0;
+  int64_t h = 0;
   std::vector<int> chans;
   void* work = nullptr;
-  cufftHandle fft = 0;
+  cufftHandle rows_all = 0, cols_half = 0, rows_half = 0, cols_all = 0;
   bool fft_ok = false;
 };
 
@@ -329,7 +334,12 @@ void free_batch(lmg_batch* b) {
     for (auto* d : k.d_desc) cudaFree(d);
   }
   for (auto& z : b->scls) {
-    if (z.fft_ok) cufftDestroy(z.fft);
+    if (z.fft_ok) {
+      cufftDestroy(z.rows_all);
+      cufftDestroy(z.cols_half);
+      cufftDestroy(z.rows_half);
+      cufftDestroy(z.cols_all);
+    }
     cudaFree(z.work);
   }
   cudaFree(b->d_img[0]);
@@ -442,11 +452,36 @@ int launch_sweeps(lmg_batch* b, int op, cudaStream_t s) {
   return LMG_OK;
 }
 
+int exec_c2c(cufftHandle plan, cufftComplex* d, int dir, cudaStream_t s) {
+  if (cufftSetStream(plan, s) != CUFFT_SUCCESS) return set_error(LMG_ECUFFT, "batch: cufftSetStream failed");
+  const cufftResult r = cufftExecC2C(plan, d, d, dir);
+  if (r != CUFFT_SUCCESS) return set_error(LMG_ECUFFT, "batch: cuFFT execution failed (code " + std::to_string(int(r)) + ")");
+  return LMG_OK;
+}
+
+// The pruned 2-D transforms of every channel's work grid (in place). Imaging (inverse):
+// every row of every channel in one call, then per channel the kept columns, which sit at
+// [0, h) and [N - h, N) in the unshifted layout. Prediction (forward): per channel the kept
+// rows (the padded model is zero elsewhere), then every column.
 int launch_ffts(lmg_batch* b, int dir, cudaStream_t s) {
   for (auto& z : b->scls) {
-    if (cufftSetStream(z.fft, s) != CUFFT_SUCCESS) return set_error(LMG_ECUFFT, "batch: cufftSetStream failed");
-    const cufftResult r = cufftExecC2C(z.fft, static_cast<cufftComplex*>(z.work), static_cast<cufftComplex*>(z.work), dir);
-    if (r != CUFFT_SUCCESS) return set_error(LMG_ECUFFT, "batch: cuFFT execution failed (code " + std::to_string(int(r)) + ")");
+    auto* w = static_cast<cufftComplex*>(z.work);
+    const size_t N = size_t(z.N), h = size_t(z.h), cells = N * N;
+    int rc = LMG_OK;
+    if (dir == CUFFT_INVERSE) {
+      rc = exec_c2c(z.rows_all, w, dir, s);
+      for (size_t j = 0; rc == LMG_OK && j < z.chans.size(); ++j) {
+        rc = exec_c2c(z.cols_half, w + j * cells, dir, s);
+        if (rc == LMG_OK) rc = exec_c2c(z.cols_half, w + j * cells + (N - h), dir, s);
+      }
+    } else {
+      for (size_t j = 0; rc == LMG_OK && j < z.chans.size(); ++j) {
+        rc = exec_c2c(z.rows_half, w + j * cells, dir, s);
+        if (rc == LMG_OK) rc = exec_c2c(z.rows_half, w + j * cells + (N - h) * N, dir, s);
+        if (rc == LMG_OK) rc = exec_c2c(z.cols_all, w + j * cells, dir, s);
+      }
+    }
+    if (rc != LMG_OK) return rc;
   }
   return LMG_OK;
 }
@@ -636,6 +671,7 @@ int lmg_batch_create(int n_chan, const lmg_table* const* tables, const int64_t* 
         b->scls.back().N = N;
       }
       b->scls[sidx[N]].chans.push_back(c);
+      b->scls[sidx[N]].h = std::max<int64_t>(b->scls[sidx[N]].h, b->plans[size_t(c)]->n_image / 2);
     }
     for (auto& z : b->scls) {
       const size_t cells = size_t(z.N) * size_t(z.N);
@@ -643,10 +679,21 @@ int lmg_batch_create(int n_chan, const lmg_table* const* tables, const int64_t* 
       if ((rc = balloc(&w, cells * z.chans.size(), "work grids"))) break;
       z.work = w;
       for (size_t j = 0; j < z.chans.size(); ++j) b->work[size_t(z.chans[j])] = w + j * cells;
-      int dims[2] = {int(z.N), int(z.N)};
-      const cufftResult fr = cufftPlanMany(&z.fft, 2, dims, nullptr, 1, int(cells), nullptr, 1, int(cells), CUFFT_C2C,
-                                           int(z.chans.size()));
+      int n1 = int(z.N);
+      const int h = int(z.h);
+      cufftResult fr = cufftPlanMany(&z.rows_all, 1, &n1, nullptr, 1, n1, nullptr, 1, n1, CUFFT_C2C,
+                                     int(z.chans.size()) * n1);
+      bool made[4] = {fr == CUFFT_SUCCESS, false, false, false};
+      if (fr == CUFFT_SUCCESS) made[1] = (fr = cufftPlanMany(&z.cols_half, 1, &n1, &n1, n1, 1, &n1, n1, 1, CUFFT_C2C, h)) ==
+                                         CUFFT_SUCCESS;
+      if (fr == CUFFT_SUCCESS) made[2] = (fr = cufftPlanMany(&z.rows_half, 1, &n1, nullptr, 1, n1, nullptr, 1, n1, CUFFT_C2C,
+                                                             h)) == CUFFT_SUCCESS;
+      if (fr == CUFFT_SUCCESS) made[3] = (fr = cufftPlanMany(&z.cols_all, 1, &n1, &n1, n1, 1, &n1, n1, 1, CUFFT_C2C, n1)) ==
+                                         CUFFT_SUCCESS;
       if (fr != CUFFT_SUCCESS) {
+        cufftHandle* hs[4] = {&z.rows_all, &z.cols_half, &z.rows_half, &z.cols_all};
+        for (int q = 0; q < 4; ++q)
+          if (made[q]) cufftDestroy(*hs[q]);
         rc = set_error(fr == CUFFT_ALLOC_FAILED ? LMG_ENOMEM : LMG_ECUFFT,
                        "batch: cufftPlanMany failed (code " + std::to_string(int(fr)) + ")");
         break;

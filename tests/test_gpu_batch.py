@@ -7,9 +7,10 @@ ragged) and weighting. A batch runs the same per-item sweep code as a single pla
 the order of float32 sums inside one bucket may differ (record ranks come from atomic
 counters), so grids and degridded visibilities agree per element within 1e-5 of the
 largest value and 1e-6 in relative RMS. Dirty images and predictions also pass through
-FFTs, which the batch runs as full batched 2-D transforms and a single plan as pruned 1-D
-transforms (different rounding), so those agree to the float32 target, 1e-5. One channel is
-also checked against the oracle at 1e-5.
+FFTs: the batch prunes them per grid size to the widest kept field among the channels of
+that size (one channel here keeps a quarter of its grid beside channels that keep half),
+a single plan to its own, so those agree to the float32 target, 1e-5. One channel is also
+checked against the oracle at 1e-5.
 """
 import ctypes
 
@@ -25,9 +26,10 @@ from tests.cases import oracle_hvec, oracle_table, rel_rms  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-# (W, N, nvis, weighted)
-CHANNELS = [(4, 512, 20000, False), (6, 256, 3001, True), (8, 1024, 60000, False), (4, 1024, 0, False),
-            (11, 512, 15000, True), (6, 512, 1, False), (8, 256, 40000, True), (4, 256, 777, False)]
+# (W, N, nvis, weighted, x0): x0 is the kept fraction, n_image = x0 N
+CHANNELS = [(4, 512, 20000, False, 0.5), (6, 256, 3001, True, 0.5), (8, 1024, 60000, False, 0.5),
+            (4, 1024, 0, False, 0.5), (11, 512, 15000, True, 0.5), (6, 512, 1, False, 0.5),
+            (8, 256, 40000, True, 0.5), (4, 256, 777, False, 0.5), (6, 512, 5000, False, 0.25)]
 MS = 1000
 
 
@@ -40,20 +42,20 @@ def close(out, ref, rms=1e-6):
 
 @pytest.fixture(scope="module")
 def setup():
-    tabs = {W: lmg.Table(W, 0.5, MS, "linear") for W in sorted({c[0] for c in CHANNELS})}
+    tabs = {(W, x0): lmg.Table(W, x0, MS, "linear") for W, x0 in sorted({(c[0], c[4]) for c in CHANNELS})}
     uvs, viss, wts, plans = [], [], [], []
-    for i, (W, N, nv, weighted) in enumerate(CHANNELS):
+    for i, (W, N, nv, weighted, x0) in enumerate(CHANNELS):
         uv = S.disk_uniform(nv, 0.45 * N, seed=100 + i)
         vis = S.complex_normal(nv, seed=100 + i).astype(np.complex64)
         w = np.random.default_rng(100 + i).uniform(0.5, 2.0, nv).astype(np.float32) if weighted else None
         uvs.append(torch.from_numpy(uv).cuda())
         viss.append(torch.from_numpy(vis).cuda())
         wts.append(torch.from_numpy(w).cuda() if w is not None else None)
-        p = lmg.Plan(tabs[W], N // 2, 1.0 / N, max(nv, 1), "c64")
+        p = lmg.Plan(tabs[(W, x0)], int(N * x0), 1.0 / N, max(nv, 1), "c64")
         p.bin(uvs[-1])
         plans.append(p)
-    batch = lmg.Batch([tabs[c[0]] for c in CHANNELS], [c[1] // 2 for c in CHANNELS], [1.0 / c[1] for c in CHANNELS],
-                      [max(c[2], 1) for c in CHANNELS])
+    batch = lmg.Batch([tabs[(c[0], c[4])] for c in CHANNELS], [int(c[1] * c[4]) for c in CHANNELS],
+                      [1.0 / c[1] for c in CHANNELS], [max(c[2], 1) for c in CHANNELS])
     batch.bin(uvs)
     return tabs, uvs, viss, wts, plans, batch
 
@@ -90,7 +92,7 @@ def test_batch_degrid_matches_single_plans(setup):
 def test_batch_dirty_image_and_predict(setup):
     tabs, uvs, viss, wts, plans, batch = setup
     imgs = batch.dirty_image(viss, wts)
-    models = [torch.from_numpy(S.gaussian_blob_image(c[1] // 2, 16, seed=40 + i).astype(np.complex64)).cuda()
+    models = [torch.from_numpy(S.gaussian_blob_image(int(c[1] * c[4]), 16, seed=40 + i).astype(np.complex64)).cuda()
               for i, c in enumerate(CHANNELS)]
     pred = batch.predict_vis(models)
     for c, p in enumerate(plans):
@@ -99,16 +101,20 @@ def test_batch_dirty_image_and_predict(setup):
             close(pred[c].cpu().numpy(), p.predict_vis(models[c]).cpu().numpy(), rms=1e-5)
 
 
-def test_batch_channel_against_oracle(setup):
+@pytest.mark.parametrize("c", [2, 8])
+def test_batch_channel_against_oracle(setup, c):
+    """Channel 2 (1024^2, half kept) and channel 8 (512^2, a quarter kept, transformed with the
+    wider pruning of its size class) against the oracle's dirty image."""
     tabs, uvs, viss, wts, plans, batch = setup
-    c = 2
-    W, N, nv, _ = CHANNELS[c]
+    W, N, nv, weighted, x0 = CHANNELS[c]
+    n = int(N * x0)
     img = batch.dirty_image(viss, wts)[c].cpu().numpy()
-    T = oracle_table(W, 0.5, MS)
-    hv = oracle_hvec(T, MS, "linear", W, N // 2, N)
+    T = oracle_table(W, x0, MS)
+    hv = oracle_hvec(T, MS, "linear", W, n, N)
     uc = I.cells_from_wavelengths(uvs[c].cpu().numpy(), N, 1.0 / N)
     op = I.Plan(uc[:, 0], uc[:, 1], W, N, single_precision_s=False)
-    ref = I.dirty_image(op, T, MS, 1, hv, N // 2, viss[c].cpu().numpy().astype(np.complex128))
+    w = wts[c].cpu().numpy().astype(np.float64) if weighted else None
+    ref = I.dirty_image(op, T, MS, 1, hv, n, viss[c].cpu().numpy().astype(np.complex128), w)
     assert rel_rms(img, ref) < 1e-5
 
 
