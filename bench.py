@@ -50,10 +50,10 @@ WORKLOAD_NAME = ("64-antenna 6 h Earth-rotation tracks (2048 samples, 1.4 GHz, d
                  "200 point sources + noise, 4096^2 grid, 2048^2 image, W=7, linear table M_s=1000, complex64")
 L2_FLUSH_BYTES = 256 << 20
 CLOCK_WINDOW_S = 2.2  # the clock record spans the timed steps plus identical steps up to this long
-VALUE_DEFINITION = ("value = visibilities / time of one whole step (bin + grid + FFT + crop/correct + pad/correct + "
-                    "FFT + degrid); grid_degrid_mvis_s = visibilities / (grid + degrid kernel time), the narrower "
-                    "figure of the metric's name")
-KERNELS_PER_STEP = 11  # bin 6, grid sweep + spill 2, crop 1, pad 1, degrid sweep 1
+VALUE_DEFINITION = ("value = visibilities / time of one whole step (bin + grid + image transform with correction "
+                    "and crop + model transform with pad and correction + degrid); grid_degrid_mvis_s = visibilities / "
+                    "(grid + degrid kernel time), the narrower figure of the metric's name")
+KERNELS_PER_STEP = 13  # bin 6, grid sweep + spill 2, image transform 2, model transform 2, degrid sweep 1
 
 
 def parse():
@@ -389,15 +389,15 @@ def accuracy(uv, dl, vis, model, img, pv):
 
 class OverlappedStep:
     """One step of the hot path through the public calls, with work that does not depend on
-    other work on separate streams: the prediction's pad + correct of the model (into a
-    workspace grid, zero outside the kept field) and its model transform (kept rows, then
-    every column) run on a side stream from the step's start, concurrently with the binning
-    and gridding on the caller's stream; after the gridding, the degridding of the
-    transformed model runs on a third stream while the caller's stream transforms and crops
-    the dirty image; the caller's stream ends the step when both are done. Nothing of step
-    k + 1 starts on any stream before step k has ended on the caller's stream.
-    Measured on the 4.1M-visibility workload: 0.982 ms per step against 1.024 ms with the
-    same calls in series (1.008 ms with the model transform alone overlapped)."""
+    other work on separate streams: the prediction's model grid (pad, correction and
+    transform: lmg_grid_from_image) runs on a side stream from the step's start,
+    concurrently with the binning and gridding on the caller's stream; after the gridding,
+    the degridding of the model grid runs on a third stream while the caller's stream
+    transforms, corrects and crops the dirty image (lmg_image_from_grid); the caller's
+    stream ends the step when both are done. The two transforms have scratch arrays of their
+    own. Nothing of step k + 1 starts on any stream before step k has ended on the caller's
+    stream. Measured on the 4.1M-visibility workload with the library transforms: 0.982 ms
+    per step against 1.024 ms with the same calls in series."""
 
     def __init__(self, plan, N, dev, tracks):
         import torch
@@ -408,6 +408,9 @@ class OverlappedStep:
         self.side2 = torch.cuda.Stream(device=dev)
         self.work = torch.empty((N, N), dtype=torch.complex64, device=dev)
         self.model_grid = torch.empty((N, N), dtype=torch.complex64, device=dev)
+        nb = plan.transform_scratch_bytes() // 8
+        self.scratch_model = torch.empty(nb, dtype=torch.complex64, device=dev) if nb else None
+        self.scratch_image = torch.empty(nb, dtype=torch.complex64, device=dev) if nb else None
         self.start = torch.cuda.Event()
         self.model_ready = torch.cuda.Event()
         self.gridded = torch.cuda.Event()
@@ -418,8 +421,7 @@ class OverlappedStep:
         self.start.record(main)
         self.side.wait_event(self.start)
         with torch.cuda.stream(self.side):
-            plan.pad_correct(model, out=self.model_grid)
-            plan.fft(self.model_grid, "model", pruned=True)
+            plan.grid_from_image(model, out=self.model_grid, scratch=self.scratch_model)
             self.model_ready.record(self.side)
         plan.bin(uv, tracks=self.tracks)
         plan.grid(vis, out=self.work)
@@ -429,8 +431,7 @@ class OverlappedStep:
         with torch.cuda.stream(self.side2):
             plan.degrid(self.model_grid, out=pv)
             self.predicted.record(self.side2)
-        plan.fft(self.work, "image", pruned=True)
-        plan.crop_correct(self.work, out=img)
+        plan.image_from_grid(self.work, out=img, scratch=self.scratch_image)
         if img_ready is not None:
             img_ready.record(main)
         main.wait_event(self.predicted)
@@ -536,11 +537,14 @@ def run_native(args):
     timed("bin_plain", lambda: plan.bin(uv_d))     # the same binning without the layout hint
     timed("bin", lambda: plan.bin(uv_d, tracks=w["tracks"]))
     timed("grid", lambda: plan.grid(vis_d, out=work))
-    timed("fft_image", lambda: plan.fft(work, "image", pruned=True))
-    timed("crop_correct", lambda: plan.crop_correct(work, out=img_d))
-    timed("pad_correct", lambda: plan.pad_correct(model_d, out=work))
-    timed("fft_model", lambda: plan.fft(work, "model", pruned=True))
+    timed("image_transform", lambda: plan.image_from_grid(work, out=img_d))     # fused, leaves work
+    timed("model_transform", lambda: plan.grid_from_image(model_d, out=work))
     timed("degrid", lambda: plan.degrid(work, out=pv_d))
+    # the library path of the same two transforms, for comparison (not in the step)
+    timed("fft_image_library", lambda: plan.fft(work, "image", pruned=True))
+    timed("crop_correct_library", lambda: plan.crop_correct(work, out=img_d))
+    timed("pad_correct_library", lambda: plan.pad_correct(model_d, out=work))
+    timed("fft_model_library", lambda: plan.fft(work, "model", pruned=True))
     # the two public calls of a step, as a whole (prediction pads only the kept rows)
     timed("dirty_image", lambda: plan.dirty_image(vis_d, out=img_d))
     timed("predict_vis", lambda: plan.predict_vis(model_d, out=pv_d))

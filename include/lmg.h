@@ -261,6 +261,28 @@ int lmg_predict_vis_ws(lmg_plan* p, const void* image, void* vis_out, void* work
 int lmg_correct_factors(int direction, const void* in, void* out, const void* h, int64_t n_image,
                         int64_t N, int dtype, void* stream);
 
+/* lmg_image_from_grid -- the dirty image from a gridded [N][N] array: the transform of
+ * Eq. 4 with the correction and crop of Eq. 15, the same result as lmg_fft_pruned
+ * (LMG_FFT_IMAGE) followed by lmg_grid_correct (LMG_CROP). For LMG_C64 plans with N = 4096
+ * it runs fused transform kernels (two launches: the rows, keeping the n_image kept columns
+ * in a scratch array, then four kept columns per CTA with the correction applied as the
+ * image is written); grid is left unchanged, image_out must be 16-byte aligned and scratch
+ * is a device array of lmg_transform_scratch_bytes bytes (16-byte aligned), or NULL for the
+ * plan's own (which concurrent calls on other streams must not share; a plan created with
+ * LMG_PLAN_NO_WORK_GRIDS has none: LMG_EINVAL). Otherwise grid is transformed in place with
+ * the library's pruned transforms and scratch is not used. */
+int lmg_image_from_grid(lmg_plan* p, void* grid, void* image_out, void* scratch, void* stream);
+
+/* lmg_grid_from_image -- the adjoint: the [N][N] grid that lmg_degrid reads for a model
+ * image (pad, correction, transform of Eq. 2), the same result as lmg_grid_correct (LMG_PAD)
+ * followed by lmg_fft_pruned (LMG_FFT_MODEL); every cell of grid_out is written. Fused
+ * kernels, alignment and scratch as for lmg_image_from_grid. */
+int lmg_grid_from_image(lmg_plan* p, const void* image, void* grid_out, void* scratch, void* stream);
+
+/* lmg_transform_scratch_bytes -- bytes of the scratch of the fused transforms
+ * (N x n_image complex64 values), or 0 where the plan uses the library transforms. */
+size_t lmg_transform_scratch_bytes(const lmg_plan* p);
+
 /* lmg_plan_status -- device status of the plan's last binning. The kernels check their own
  * bounds and record what they could not do in a status word instead of faulting (today:
  * more work items than the plan's capacity, whose excess is dropped; the capacity is sized

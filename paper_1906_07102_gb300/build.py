@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "liblmg.so")
-SOURCES = ["api.cu", "bin.cu", "sweep.cu", "sweep_ext.cu", "batch.cu", "correct.cu", "static_grid.cu", "peak.cu",
+SOURCES = ["api.cu", "bin.cu", "sweep.cu", "sweep_ext.cu", "batch.cu", "correct.cu", "static_grid.cu", "peak.cu", "fft.cu",
            "table.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -86,7 +86,7 @@ namespace lmg {
 void free_plan(lmg_plan* p) {
   if (!p) return;
   void* ptrs[] = {p->d_table, p->d_h, p->hist, p->offsets, p->rank, p->partial, p->recs,
-                  p->items, p->counters, p->spill, p->frac, p->work, p->model};
+                  p->items, p->counters, p->spill, p->frac, p->work, p->model, p->d_tw, p->xform_tmp};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->fft_ok) cufftDestroy(p->fft);
@@ -242,6 +242,31 @@ int fft_model_pruned(lmg_plan* p, void* g, cudaStream_t st) {
   return rc;
 }
 
+// The dirty image from a gridded array (Eq. 4, correction and crop of Eq. 15): the fused
+// transform kernels where the plan has them (the grid is left as it is), else the pruned
+// library transform in place followed by the crop kernel.
+int image_from_grid(lmg_plan* p, void* grid, void* image, void* scratch, cudaStream_t st) {
+  if (p->xform)
+    return launch_status(xform_image_launch(grid, image, scratch, static_cast<const float*>(p->d_h), p->d_tw,
+                                            int(p->n_image), st),
+                         "image transform");
+  int rc = fft_image_pruned(p, grid, st);
+  if (rc == LMG_OK)
+    rc = launch_status(crop_correct_launch(grid, image, p->d_h, int(p->n_image), int(p->N), p->dtype, st), "crop");
+  return rc;
+}
+
+// The model grid from an image (pad and correction, transform of Eq. 2).
+int grid_from_image(lmg_plan* p, const void* image, void* grid, void* scratch, cudaStream_t st) {
+  if (p->xform)
+    return launch_status(xform_model_launch(image, grid, scratch, static_cast<const float*>(p->d_h), p->d_tw,
+                                            int(p->n_image), st),
+                         "model transform");
+  int rc = launch_status(pad_correct_launch(image, grid, p->d_h, int(p->n_image), int(p->N), p->dtype, st), "pad");
+  if (rc == LMG_OK) rc = fft_model_pruned(p, grid, st);
+  return rc;
+}
+
 }  // namespace
 
 namespace lmg {
@@ -320,6 +345,9 @@ int plan_create(const lmg_table* t, int64_t n_image, double pixel_scale, int64_t
     if (rs == 8) reinterpret_cast<double*>(h_bytes.data())[q] = hcorr[size_t(q)];
     else reinterpret_cast<float*>(h_bytes.data())[q] = float(hcorr[size_t(q)]);
   }
+  // fused kept-field transforms where they apply (complex64, N = 4096; the work and model
+  // grids of the plan path then need no separate model grid)
+  p->xform = opt.fft && xform_supported(dtype, N, n_image);
   const size_t c2 = 2 * rs;
   if ((rc = dalloc(reinterpret_cast<unsigned char**>(&p->d_table), tab_bytes.size(), "table")) ||
       (rc = dalloc(reinterpret_cast<unsigned char**>(&p->d_h), h_bytes.size(), "correction")) ||
@@ -330,7 +358,11 @@ int plan_create(const lmg_table* t, int64_t n_image, double pixel_scale, int64_t
       (rc = dalloc(reinterpret_cast<unsigned char**>(&p->spill), size_t(p->item_cap) * ring_slots(p->W) * strip * c2, "spill")) ||
       (dtype == LMG_C128 && (rc = dalloc(&p->frac, size_t(max_vis), "quantisation residuals"))) ||
       (opt.work_grid && (rc = dalloc(reinterpret_cast<unsigned char**>(&p->work), size_t(N) * size_t(N) * c2, "work grid"))) ||
-      (opt.work_grid && (rc = dalloc(reinterpret_cast<unsigned char**>(&p->model), size_t(N) * size_t(N) * c2, "model grid")))) {
+      (opt.work_grid && !p->xform &&
+       (rc = dalloc(reinterpret_cast<unsigned char**>(&p->model), size_t(N) * size_t(N) * c2, "model grid"))) ||
+      (p->xform && (rc = dalloc(reinterpret_cast<unsigned char**>(&p->d_tw), size_t(kXformN) * 8, "twiddles"))) ||
+      (p->xform && opt.work_grid &&
+       (rc = dalloc(reinterpret_cast<unsigned char**>(&p->xform_tmp), xform_scratch_bytes(n_image), "transform scratch")))) {
     free_plan(p);
     return rc;
   }
@@ -341,7 +373,17 @@ int plan_create(const lmg_table* t, int64_t n_image, double pixel_scale, int64_t
     free_plan(p);
     return cuda_error(e, "device query");
   }
-  if ((e = cudaMemcpy(p->d_table, tab_bytes.data(), tab_bytes.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+  std::vector<float> tw;
+  if (p->xform) {
+    tw.resize(2 * size_t(kXformN));
+    for (int k = 0; k < kXformN; ++k) {
+      const double a = 2.0 * 3.14159265358979323846 * k / kXformN;
+      tw[2 * size_t(k)] = float(std::cos(a));
+      tw[2 * size_t(k) + 1] = float(std::sin(a));
+    }
+  }
+  if ((p->xform && (e = cudaMemcpy(p->d_tw, tw.data(), tw.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess) ||
+      (e = cudaMemcpy(p->d_table, tab_bytes.data(), tab_bytes.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(p->d_h, h_bytes.data(), h_bytes.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemset(p->counters, 0, kNumCounters * sizeof(int))) != cudaSuccess ||
       (p->model && (e = cudaMemset(p->model, 0, size_t(N) * size_t(N) * c2)) != cudaSuccess)) {
@@ -373,6 +415,10 @@ int plan_create(const lmg_table* t, int64_t n_image, double pixel_scale, int64_t
     return cuda_error(cudaGetLastError(), "sweep kernel attributes");
   }
   p->blocks_degrid = p->sms * (bps > 0 ? bps : 1);
+  if (p->xform && xform_set_limits() != 0) {
+    free_plan(p);
+    return cuda_error(cudaGetLastError(), "transform kernel attributes");
+  }
   if (opt.fft) {
     if (inject_fault("cufft_plan")) {
       free_plan(p);
@@ -668,14 +714,11 @@ int lmg_dirty_image(lmg_plan* p, const void* vis, const void* weights, int accum
   if (accum != LMG_ACCUM_PLAIN && accum != LMG_ACCUM_COMPENSATED) return set_error(LMG_EINVAL, "bad accum");
   if (accum == LMG_ACCUM_COMPENSATED && p->dtype != LMG_C64)
     return set_error(LMG_EUNSUPPORTED, "compensated accumulation is for LMG_C64");
-  if (int rc = need_aligned(image_out, elem_bytes(p->dtype), "image")) return rc;
+  if (int rc = need_aligned(image_out, p->xform ? 16 : elem_bytes(p->dtype), "image")) return rc;
   if (int rc = need_vis_aligned(p, vis, weights)) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int rc = do_grid(p, vis, weights, accum, p->work, st);
-  if (rc == LMG_OK) rc = fft_image_pruned(p, p->work, st);
-  if (rc == LMG_OK)
-    rc = launch_status(crop_correct_launch(p->work, image_out, p->d_h, int(p->n_image), int(p->N), p->dtype, st),
-                       "crop");
+  if (rc == LMG_OK) rc = image_from_grid(p, p->work, image_out, p->xform_tmp, st);
   return rc;
 }
 
@@ -685,11 +728,18 @@ int lmg_predict_vis(lmg_plan* p, const void* image, void* vis_out, void* stream)
   if (int rc = need_binned(p)) return rc;
   if (!p->work) return set_error(LMG_EINVAL, "plan has no work grids (LMG_PLAN_NO_WORK_GRIDS): use lmg_predict_vis_ws");
   if (p->nvis > 0 && !vis_out) return set_error(LMG_EINVAL, "vis_out is NULL");
-  if (int rc = need_aligned(image, elem_bytes(p->dtype), "image")) return rc;
+  if (int rc = need_aligned(image, p->xform ? 16 : elem_bytes(p->dtype), "image")) return rc;
   if (int rc = need_vis_aligned(p, vis_out, nullptr)) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int rc = launch_status(pad_rows_launch(image, p->model, p->d_h, int(p->n_image), int(p->N), p->dtype, st), "pad");
-  if (rc == LMG_OK) rc = fft_model_to_work(p, st);
+  int rc;
+  if (p->xform) {
+    rc = launch_status(xform_model_launch(image, p->work, p->xform_tmp, static_cast<const float*>(p->d_h), p->d_tw,
+                                          int(p->n_image), st),
+                       "model transform");
+  } else {
+    rc = launch_status(pad_rows_launch(image, p->model, p->d_h, int(p->n_image), int(p->N), p->dtype, st), "pad");
+    if (rc == LMG_OK) rc = fft_model_to_work(p, st);
+  }
   if (rc == LMG_OK) rc = do_degrid(p, p->work, vis_out, st);
   return rc;
 }
@@ -773,6 +823,40 @@ int lmg_correct_factors(int direction, const void* in, void* out, const void* h,
   else if (direction == LMG_PAD) rc = pad_correct_launch(in, out, h, int(n_image), int(N), dtype, st);
   else return set_error(LMG_EINVAL, "direction must be LMG_CROP or LMG_PAD");
   return launch_status(rc, "grid correction");
+}
+
+size_t lmg_transform_scratch_bytes(const lmg_plan* p) {
+  if (!p || !p->xform) return 0;
+  return xform_scratch_bytes(p->n_image);
+}
+
+namespace {
+int check_transform_args(lmg_plan* p, const void* grid, const void* image, void* scratch) {
+  if (!p || !grid || !image) return set_error(LMG_EINVAL, "NULL argument");
+  if (!p->fft_pruned_ok) return set_error(LMG_EUNSUPPORTED, "plan has no FFT plans");
+  if (int rc = need_aligned(grid, 16, "grid")) return rc;
+  // the fused kernels move four pixels (32 bytes) at a time
+  if (int rc = need_aligned(image, p->xform ? 16 : elem_bytes(p->dtype), "image")) return rc;
+  if (p->xform) {
+    if (!scratch && !p->xform_tmp)
+      return set_error(LMG_EINVAL, "plan has no transform scratch (LMG_PLAN_NO_WORK_GRIDS): pass one of "
+                                   "lmg_transform_scratch_bytes bytes");
+    if (int rc = need_aligned(scratch, 16, "scratch")) return rc;
+  }
+  return LMG_OK;
+}
+}  // namespace
+
+int lmg_image_from_grid(lmg_plan* p, void* grid, void* image_out, void* scratch, void* stream) {
+  clear_error();
+  if (int rc = check_transform_args(p, grid, image_out, scratch)) return rc;
+  return image_from_grid(p, grid, image_out, scratch ? scratch : p->xform_tmp, static_cast<cudaStream_t>(stream));
+}
+
+int lmg_grid_from_image(lmg_plan* p, const void* image, void* grid_out, void* scratch, void* stream) {
+  clear_error();
+  if (int rc = check_transform_args(p, grid_out, image, scratch)) return rc;
+  return grid_from_image(p, image, grid_out, scratch ? scratch : p->xform_tmp, static_cast<cudaStream_t>(stream));
 }
 
 int lmg_plan_status(lmg_plan* p, int* status_bits, void* stream) {

@@ -60,6 +60,16 @@ struct BinArgs {
                      // samples that share a bucket. 0: no order assumed.
 };
 
+// Fused kept-field transforms (fft.cu): complex64 plans with N = kXformN only.
+constexpr int kXformN = 4096;
+bool xform_supported(int dtype, long long N, long long n);
+size_t xform_scratch_bytes(long long n);
+int xform_set_limits();
+int xform_image_launch(const void* grid, void* image, void* scratch, const float* h, const void* tw, int n,
+                       cudaStream_t st);
+int xform_model_launch(const void* image, void* grid, void* scratch, const float* h, const void* tw, int n,
+                       cudaStream_t st);
+
 int bin_launch(const BinArgs& a, cudaStream_t st);
 int bin_scan_chunks(long long L);
 

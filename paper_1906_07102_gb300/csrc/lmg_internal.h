@@ -89,6 +89,11 @@ struct lmg_plan {
   // the n_image / 2 rows at either end, all columns, the n_image / 2 columns at either end
   cufftHandle fft_rows_all = 0, fft_rows_half = 0, fft_cols_all = 0, fft_cols_half = 0;
   bool fft_pruned_ok = false;
+  // fused kept-field transforms (complex64, N = 4096): twiddle table e(k / 4096) and the
+  // plan's own scratch (N x n_image values; null without work grids)
+  bool xform = false;
+  void* d_tw = nullptr;
+  void* xform_tmp = nullptr;
 };
 
 namespace lmg {

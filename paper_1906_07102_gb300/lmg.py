@@ -35,6 +35,9 @@ _SIGS = {
     "lmg_plan_free": (ctypes.c_int, [_vp]),
     "lmg_plan_bin": (ctypes.c_int, [_vp, _vp, _i64, _vp]),
     "lmg_plan_bin_tracks": (ctypes.c_int, [_vp, _vp, _i64, _i64, _vp]),
+    "lmg_transform_scratch_bytes": (ctypes.c_size_t, [_vp]),
+    "lmg_image_from_grid": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "lmg_grid_from_image": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "lmg_plan_dropped": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), _vp]),
     "lmg_plan_info": (ctypes.c_int, [_vp, _vp, _vp]),
     "lmg_work_grid": (_vp, [_vp]),
@@ -186,6 +189,31 @@ class Plan:
             _check(lib().lmg_plan_bin_tracks(self._h, _ptr(uv), uv.shape[0], int(tracks), _stream()))
         self.nvis = uv.shape[0]
         return self
+
+    def transform_scratch_bytes(self):
+        """Bytes of the scratch of image_from_grid / grid_from_image (0: none needed)."""
+        return int(lib().lmg_transform_scratch_bytes(self._h))
+
+    def image_from_grid(self, grid, out=None, scratch=None):
+        """Dirty image from a gridded [N, N] array: transform, correction and crop (the
+        fused kernels where the plan has them; otherwise grid is transformed in place)."""
+        import torch
+        _need(grid, self.cdtype, (self.N, self.N), "grid")
+        if out is None:
+            out = torch.empty((self.n_image, self.n_image), dtype=self.cdtype, device=grid.device)
+        _need(out, self.cdtype, (self.n_image, self.n_image), "image")
+        _check(lib().lmg_image_from_grid(self._h, _ptr(grid), _ptr(out), _ptr(scratch), _stream()))
+        return out
+
+    def grid_from_image(self, image, out=None, scratch=None):
+        """Model grid [N, N] from an image: pad, correction and transform."""
+        import torch
+        _need(image, self.cdtype, (self.n_image, self.n_image), "image")
+        if out is None:
+            out = torch.empty((self.N, self.N), dtype=self.cdtype, device=image.device)
+        _need(out, self.cdtype, (self.N, self.N), "grid")
+        _check(lib().lmg_grid_from_image(self._h, _ptr(image), _ptr(out), _ptr(scratch), _stream()))
+        return out
 
     def _vis_args(self, vis, weights):
         vis = _need(vis, self.cdtype, (self.nvis,), "vis")
