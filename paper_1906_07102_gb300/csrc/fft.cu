@@ -36,10 +36,9 @@ constexpr int kPitchA = 264;       // first exchange: 16 rows of 256 values (+8:
 constexpr int kPitchB = 17;        // second exchange: 256 rows of 16 values (+1)
 constexpr int kBuf = 256 * kPitchB;  // elements of one transform's exchange buffer (>= 16 kPitchA)
 static_assert(kBuf >= 16 * kPitchA, "exchange buffer");
-constexpr int kBW = 4;             // columns per scratch block (one column CTA each)
-constexpr int kColGroups = 2;      // transforms a column CTA runs at a time (kBW / kColGroups passes)
-constexpr int kColThreads = kColGroups * kT;
-constexpr int kColMinBlocks = 2;   // resident column CTAs per SM (70 KB of shared memory each)
+constexpr int kBW = 4;             // columns per scratch block = transforms per column CTA
+constexpr int kColThreads = kBW * kT;
+constexpr int kColMinBlocks = kBW == 4 ? 1 : (kBW == 2 ? 2 : 3);  // resident CTAs per SM
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -180,12 +179,8 @@ __global__ void __launch_bounds__(kT) k_image_rows(const float2* __restrict__ G,
   }
 }
 
-// Imaging, columns: one block of kBW kept columns per CTA, kColGroups transforms (+i) at a
-// time, each by 256 threads straight from the scratch (the block's columns share 32-byte
-// sectors, read by neighbouring groups and passes); the kept rows corrected (h(x) h(y) and
-// the centring sign (-1)^(qx + qy)) and written to the image pixel by pixel (the image is
-// small enough for L2 to gather the pieces of a sector). Only the exchange buffers are in
-// shared memory, so two CTAs share an SM and one's loads overlap the other's transforms.
+// Imaging, columns: kBW kept columns per CTA (256 threads each) transformed (+i), their
+// kept rows corrected (h(x) h(y) and the centring sign (-1)^(qx + qy)) into the image.
 __global__ void __launch_bounds__(kColThreads, kColMinBlocks)
     k_image_cols(const float2* __restrict__ T, float2* __restrict__ img, const float* __restrict__ h,
                  const float2* __restrict__ tw, int n) {
@@ -194,31 +189,54 @@ __global__ void __launch_bounds__(kColThreads, kColMinBlocks)
   load_twiddles(tw, stw);
   const int b = blockIdx.x, g = threadIdx.x >> 8, t = threadIdx.x & (kT - 1), half = n / 2;
   float2* buf = sm + g * kBuf;
-  const float2* blk = T + static_cast<size_t>(b) * kN * kBW;
-#pragma unroll 1
-  for (int pass = 0; pass < kBW / kColGroups; ++pass) {
-    const int c = pass * kColGroups + g, q = kBW * b + c, qx = q - half;
-    float2 v[16];
+  // the block (4096 rows x kBW columns, contiguous) into kBW column buffers, two values per load
+  const float4* blk = reinterpret_cast<const float4*>(T + static_cast<size_t>(b) * kN * kBW);
+  for (int c = threadIdx.x; c < kN * kBW / 2; c += kColThreads) {
+    const float4 x = __ldcs(blk + c);
+    const int e = 2 * c;
+    sm[(e % kBW) * kBuf + e / kBW] = make_float2(x.x, x.y);
+    sm[((e + 1) % kBW) * kBuf + (e + 1) / kBW] = make_float2(x.z, x.w);
+  }
+  __syncthreads();
+  float2 v[16];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = blk[(t + 256 * j) * kBW + c];
-    __syncthreads();  // the twiddles (first pass) and the previous pass's buffer reads
-    fft4096<1>(v, buf, stw, t, BlockSync{});
-    const float hx = h[q];
+  for (int j = 0; j < 16; ++j) v[j] = buf[t + 256 * j];
+  __syncthreads();
+  fft4096<1>(v, buf, stw, t, BlockSync{});
+  __syncthreads();
 #pragma unroll
-    for (int k2 = 0; k2 < 16; ++k2) {
-      const int r = kept_slot(t + 256 * k2, half);
-      if (r >= 0) {
-        float f = hx * h[r];
-        if ((qx + r - half) & 1) f = -f;
-        img[static_cast<size_t>(r) * n + q] = make_float2(f * v[k2].x, f * v[k2].y);
-      }
+  for (int k2 = 0; k2 < 16; ++k2) {
+    const int r = kept_slot(t + 256 * k2, half);
+    if (r >= 0) buf[r] = v[k2];
+  }
+  __syncthreads();
+  // kept rows r of the columns kBW b .. kBW b + kBW - 1: one kBW x 8-byte piece per row
+  const int q0 = kBW * b;
+  for (int r = threadIdx.x; r < n; r += kColThreads) {
+    const int qy = r - half;
+    const float hy = h[r];
+    float2 o[kBW];
+#pragma unroll
+    for (int c = 0; c < kBW; ++c) {
+      const int qx = q0 + c - half;
+      float f = h[q0 + c] * hy;
+      if ((qx + qy) & 1) f = -f;
+      const float2 x = sm[c * kBuf + r];
+      o[c] = make_float2(f * x.x, f * x.y);
+    }
+    float2* dst = img + static_cast<size_t>(r) * n + q0;
+    if constexpr (kBW == 1) {
+      dst[0] = o[0];
+    } else {
+#pragma unroll
+      for (int c = 0; c < kBW; c += 2)
+        *reinterpret_cast<float4*>(dst + c) = make_float4(o[c].x, o[c].y, o[c + 1].x, o[c + 1].y);
     }
   }
 }
 
-// Prediction, columns: one block of kBW image columns per CTA, kColGroups at a time:
-// corrected, placed at their kept rows of a zero column of 4096 (in registers), transformed
-// (-i) and written to the scratch block (all 4096 rows).
+// Prediction, columns: kBW image columns per CTA corrected, placed at their kept rows of
+// a zero column of 4096 and transformed (-i) into the scratch (all 4096 rows).
 __global__ void __launch_bounds__(kColThreads, kColMinBlocks)
     k_model_cols(const float2* __restrict__ img, float2* __restrict__ T, const float* __restrict__ h,
                  const float2* __restrict__ tw, int n) {
@@ -227,27 +245,48 @@ __global__ void __launch_bounds__(kColThreads, kColMinBlocks)
   load_twiddles(tw, stw);
   const int b = blockIdx.x, g = threadIdx.x >> 8, t = threadIdx.x & (kT - 1), half = n / 2;
   float2* buf = sm + g * kBuf;
-  float2* blk = T + static_cast<size_t>(b) * kN * kBW;
-#pragma unroll 1
-  for (int pass = 0; pass < kBW / kColGroups; ++pass) {
-    const int c = pass * kColGroups + g, q = kBW * b + c, qx = q - half;
-    const float hx = h[q];
-    float2 v[16];
+  const int q0 = kBW * b;
+  for (int i = threadIdx.x; i < kBW * kN; i += kColThreads) sm[(i >> 12) * kBuf + (i & (kN - 1))] = make_float2(0.f, 0.f);
+  __syncthreads();
+  for (int r = threadIdx.x; r < n; r += kColThreads) {
+    const int qy = r - half, iy = qy < 0 ? qy + kN : qy;
+    const float hy = h[r];
+    const float2* src = img + static_cast<size_t>(r) * n + q0;
+    float2 x[kBW];
+    if constexpr (kBW == 1) {
+      x[0] = src[0];
+    } else {
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const int r = kept_slot(t + 256 * j, half);  // image row at grid row t + 256 j
-      v[j] = make_float2(0.f, 0.f);
-      if (r >= 0) {
-        const float2 x = img[static_cast<size_t>(r) * n + q];
-        float f = hx * h[r];
-        if ((qx + r - half) & 1) f = -f;
-        v[j] = make_float2(f * x.x, f * x.y);
+      for (int c = 0; c < kBW; c += 2) {
+        const float4 a = *reinterpret_cast<const float4*>(src + c);
+        x[c] = make_float2(a.x, a.y);
+        x[c + 1] = make_float2(a.z, a.w);
       }
     }
-    __syncthreads();
-    fft4096<-1>(v, buf, stw, t, BlockSync{});
 #pragma unroll
-    for (int k2 = 0; k2 < 16; ++k2) blk[(t + 256 * k2) * kBW + c] = v[k2];
+    for (int c = 0; c < kBW; ++c) {
+      const int qx = q0 + c - half;
+      float f = h[q0 + c] * hy;
+      if ((qx + qy) & 1) f = -f;
+      sm[c * kBuf + iy] = make_float2(f * x[c].x, f * x[c].y);
+    }
+  }
+  __syncthreads();
+  float2 v[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = buf[t + 256 * j];
+  __syncthreads();
+  fft4096<-1>(v, buf, stw, t, BlockSync{});
+  __syncthreads();
+#pragma unroll
+  for (int k2 = 0; k2 < 16; ++k2) buf[t + 256 * k2] = v[k2];
+  __syncthreads();
+  // the block, contiguous, two values per store
+  float4* blk = reinterpret_cast<float4*>(T + static_cast<size_t>(b) * kN * kBW);
+  for (int c = threadIdx.x; c < kN * kBW / 2; c += kColThreads) {
+    const int e = 2 * c;
+    const float2 x0 = sm[(e % kBW) * kBuf + e / kBW], x1 = sm[((e + 1) % kBW) * kBuf + (e + 1) / kBW];
+    blk[c] = make_float4(x0.x, x0.y, x1.x, x1.y);
   }
 }
 
@@ -272,7 +311,7 @@ __global__ void __launch_bounds__(kT) k_model_rows(const float2* __restrict__ T,
   for (int k2 = 0; k2 < 16; ++k2) dst[t + 256 * k2] = v[k2];
 }
 
-constexpr size_t kColSmem = size_t(kColGroups) * kBuf * sizeof(float2);
+constexpr size_t kColSmem = size_t(kBW) * kBuf * sizeof(float2);
 
 }  // namespace
 
