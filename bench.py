@@ -395,7 +395,8 @@ class OverlappedStep:
     the degridding of the model grid runs on a third stream while the caller's stream
     transforms, corrects and crops the dirty image (lmg_image_from_grid); the caller's
     stream ends the step when both are done. The two transforms have scratch arrays of their
-    own. Nothing of step k + 1 starts on any stream before step k has ended on the caller's
+    own; the predictions' buffer is zeroed on the side stream at the start and the
+    degridding adds into it (lmg_degrid_add), so that no zeroing precedes it. Nothing of step k + 1 starts on any stream before step k has ended on the caller's
     stream. Measured on the 4.1M-visibility workload with the library transforms: 0.982 ms
     per step against 1.024 ms with the same calls in series."""
 
@@ -421,6 +422,7 @@ class OverlappedStep:
         self.start.record(main)
         self.side.wait_event(self.start)
         with torch.cuda.stream(self.side):
+            pv.zero_()   # the degridding adds into it (lmg_degrid_add): no zeroing on the critical path
             plan.grid_from_image(model, out=self.model_grid, scratch=self.scratch_model)
             self.model_ready.record(self.side)
         plan.bin(uv, tracks=self.tracks)
@@ -429,7 +431,7 @@ class OverlappedStep:
         self.side2.wait_event(self.gridded)
         self.side2.wait_event(self.model_ready)
         with torch.cuda.stream(self.side2):
-            plan.degrid(self.model_grid, out=pv)
+            plan.degrid(self.model_grid, out=pv, add=True)
             self.predicted.record(self.side2)
         plan.image_from_grid(self.work, out=img, scratch=self.scratch_image)
         if img_ready is not None:

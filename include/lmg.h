@@ -197,6 +197,12 @@ int lmg_grid(lmg_plan* p, const void* vis, const void* weights, int accum, void*
  * vis_out: device complex [nvis], every entry overwritten. Allocates nothing. */
 int lmg_degrid(lmg_plan* p, const void* grid, void* vis_out, void* stream);
 
+/* lmg_degrid_add -- lmg_degrid that adds the predictions to vis_inout instead of
+ * overwriting it (Section 4; e.g. the sum of the predictions from several grids, or an
+ * output zeroed earlier on another stream). Dropped positions leave their entries as they
+ * are. Same arguments, alignment and errors as lmg_degrid. */
+int lmg_degrid_add(lmg_plan* p, const void* grid, void* vis_inout, void* stream);
+
 /* lmg_fft -- unnormalised in-place 2-D FFT of a device grid [N][N] in grid index order.
  * direction LMG_FFT_IMAGE computes sum_i G[i] exp(+i 2 pi i q / N) (cuFFT inverse);
  * LMG_FFT_MODEL computes sum_q P[q] exp(-i 2 pi i q / N) (cuFFT forward). */

@@ -165,14 +165,14 @@ int do_grid(lmg_plan* p, const void* vis, const void* weights, int accum, void* 
   return launch_status(grid_launch(a, st), "gridding");
 }
 
-int do_degrid(lmg_plan* p, const void* grid, void* vis_out, cudaStream_t st) {
+int do_degrid(lmg_plan* p, const void* grid, void* vis_out, cudaStream_t st, bool add = false) {
   SweepArgs a = sweep_args(p);
   a.grid_in = grid;
   a.vis_out = vis_out;
   a.grid_blocks = p->blocks_degrid;
   a.warps = p->warps_degrid;
   a.table_in_smem = p->tab_smem_degrid ? 1 : 0;
-  return launch_status(degrid_launch(a, st), "degridding");
+  return launch_status(degrid_launch(a, st, !add), "degridding");
 }
 
 int do_fft(lmg_plan* p, int direction, void* g, cudaStream_t st) {
@@ -672,6 +672,16 @@ int lmg_degrid(lmg_plan* p, const void* grid, void* vis_out, void* stream) {
   if (int rc = need_aligned(grid, 16, "grid")) return rc;
   if (int rc = need_vis_aligned(p, vis_out, nullptr)) return rc;
   return do_degrid(p, grid, vis_out, static_cast<cudaStream_t>(stream));
+}
+
+int lmg_degrid_add(lmg_plan* p, const void* grid, void* vis_inout, void* stream) {
+  clear_error();
+  if (!p || !grid) return set_error(LMG_EINVAL, "NULL argument");
+  if (int rc = need_binned(p)) return rc;
+  if (p->nvis > 0 && !vis_inout) return set_error(LMG_EINVAL, "vis_inout is NULL");
+  if (int rc = need_aligned(grid, 16, "grid")) return rc;
+  if (int rc = need_vis_aligned(p, vis_inout, nullptr)) return rc;
+  return do_degrid(p, grid, vis_inout, static_cast<cudaStream_t>(stream), true);
 }
 
 int lmg_fft(lmg_plan* p, int direction, void* grid, void* stream) {

@@ -126,44 +126,26 @@ __global__ void k_scan_partials(const int* __restrict__ in, long long n, int* __
   }
 }
 
-// Stage 2: exclusive scan of the chunk sums in one block (sequential over tiles of 1024).
-__global__ void k_scan_top(int* __restrict__ partial, int nchunks) {
-  __shared__ int carry;
-  __shared__ int warp_sums[32];
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  for (int base = 0; base < nchunks; base += blockDim.x) {
-    const int i = base + threadIdx.x;
-    const int v = i < nchunks ? partial[i] : 0;
-    int x = v;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_sums[w] = x;
-    __syncthreads();
-    if (w == 0) {
-      int ws = lane < (blockDim.x >> 5) ? warp_sums[lane] : 0;
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, ws, o);
-        if (lane >= o) ws += y;
-      }
-      warp_sums[lane] = ws;
-    }
-    __syncthreads();
-    const int incl = x + (w > 0 ? warp_sums[w - 1] : 0);
-    if (i < nchunks) partial[i] = carry + incl - v;
-    __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) carry += incl;
-    __syncthreads();
-  }
-}
-
-// Stage 3: exclusive scan within each chunk plus the chunk offset; writes offsets[0..n].
+// Stage 2: exclusive scan within each chunk plus the chunk's offset, the sum of the
+// preceding chunks' totals (each CTA adds them up itself: a few thousand at most, cheaper
+// than a separate launch); writes offsets[0..n].
 __global__ void k_scan_final(const int* __restrict__ in, long long n, const int* __restrict__ partial,
                              int* __restrict__ offsets) {
   __shared__ int warp_sums[kScanThreads / 32];
+  __shared__ int chunk_base;
+  {
+    int c = 0;
+    for (int k = threadIdx.x; k < static_cast<int>(blockIdx.x); k += blockDim.x) c += partial[k];
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int t = 0;
+      for (int w = 0; w < kScanThreads / 32; ++w) t += warp_sums[w];
+      chunk_base = t;
+    }
+    __syncthreads();
+  }
   const long long base = static_cast<long long>(blockIdx.x) * kScanChunk + threadIdx.x * kScanPer;
   int v[kScanPer];
   int s = 0;
@@ -182,7 +164,7 @@ __global__ void k_scan_final(const int* __restrict__ in, long long n, const int*
   __syncthreads();
   int woff = 0;
   for (int k = 0; k < w; ++k) woff += warp_sums[k];
-  int run = partial[blockIdx.x] + woff + x - s;
+  int run = chunk_base + woff + x - s;
 #pragma unroll
   for (int i = 0; i < kScanPer; ++i) {
     if (base + i < n) offsets[base + i] = run;
@@ -480,7 +462,6 @@ int bin_launch(const BinArgs& a, cudaStream_t st) {
                                             a.hist, a.counters, a.frac);
   const int nchunks = static_cast<int>((L + kScanChunk - 1) / kScanChunk);
   k_scan_partials<<<nchunks, kScanThreads, 0, st>>>(a.hist, L, a.partial);
-  k_scan_top<<<1, 1024, 0, st>>>(a.partial, nchunks);
   k_scan_final<<<nchunks, kScanThreads, 0, st>>>(a.hist, L, a.partial, a.offsets);
   if (a.tracks > 0)
     k_bin_scatter_tracks<<<blocks_t, threads, 0, st>>>(a.uv, a.scale2, a.rank, a.nvis, a.tracks, a.W, a.N,

@@ -103,7 +103,8 @@ struct SweepArgs {
 int grid_launch(const SweepArgs& a, cudaStream_t st);
 // Rows held in the sweep's rolling ring for support W (spill buffer rows per item).
 int ring_slots(int W);
-int degrid_launch(const SweepArgs& a, cudaStream_t st);
+// zero_out: zero the outputs first (else the predictions are added to what is there)
+int degrid_launch(const SweepArgs& a, cudaStream_t st, bool zero_out = true);
 // Shared memory a sweep CTA needs (bytes) and CTAs per SM that fit; used to size launches.
 size_t sweep_smem_bytes(int W, int dtype, int Ms, bool table_in_smem, bool degrid, int warps);
 // ext: the kernels of the extended lookups (interp >= 2: Lagrange, direct calculation).

@@ -83,12 +83,12 @@ int grid_launch(const SweepArgs& a, cudaStream_t st) {
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int degrid_launch(const SweepArgs& a, cudaStream_t st) {
+int degrid_launch(const SweepArgs& a, cudaStream_t st, bool zero_out) {
   void* k = kernel_for(a.W, a.dtype, 0, true, a.interp >= 2);
   if (!k) return -1;
   const size_t smem = sweep_smem_bytes(a.W, a.dtype, a.Ms, a.table_in_smem != 0, true, a.warps);
   // outputs start at zero: each record adds its partial sum (dropped positions stay zero)
-  if (a.nvis > 0) cudaMemsetAsync(a.vis_out, 0, size_t(a.nvis) * (a.dtype ? 16 : 8), st);
+  if (zero_out && a.nvis > 0) cudaMemsetAsync(a.vis_out, 0, size_t(a.nvis) * (a.dtype ? 16 : 8), st);
   cudaMemsetAsync(a.counters + kCntDegridWork, 0, sizeof(int), st);
   SweepArgs args = a;
   void* params[] = {&args};

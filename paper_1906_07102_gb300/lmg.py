@@ -36,6 +36,7 @@ _SIGS = {
     "lmg_plan_bin": (ctypes.c_int, [_vp, _vp, _i64, _vp]),
     "lmg_plan_bin_tracks": (ctypes.c_int, [_vp, _vp, _i64, _i64, _vp]),
     "lmg_transform_scratch_bytes": (ctypes.c_size_t, [_vp]),
+    "lmg_degrid_add": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "lmg_image_from_grid": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "lmg_grid_from_image": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "lmg_plan_dropped": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), _vp]),
@@ -230,13 +231,17 @@ class Plan:
         _check(lib().lmg_grid(self._h, _ptr(vis), _ptr(weights), ACCUM[accum], _ptr(out), _stream()))
         return out
 
-    def degrid(self, grid, out=None):
+    def degrid(self, grid, out=None, add=False):
+        """Predicted visibilities of a grid; add=True adds them to out (lmg_degrid_add)."""
         import torch
         _need(grid, self.cdtype, (self.N, self.N), "grid")
         if out is None:
+            if add:
+                raise ValueError("add=True needs out")
             out = torch.empty(self.nvis, dtype=self.cdtype, device=grid.device)
         _need(out, self.cdtype, (self.nvis,), "vis_out")
-        _check(lib().lmg_degrid(self._h, _ptr(grid), _ptr(out), _stream()))
+        f = lib().lmg_degrid_add if add else lib().lmg_degrid
+        _check(f(self._h, _ptr(grid), _ptr(out), _stream()))
         return out
 
     def fft(self, grid, direction, pruned=False):

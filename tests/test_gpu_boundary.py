@@ -144,3 +144,18 @@ def test_misaligned_views_are_rejected(case):
     # the plan still works after the refusals
     g = p.grid(visd)
     assert torch.isfinite(torch.view_as_real(g)).all()
+
+
+def test_degrid_add_accumulates(case):
+    """lmg_degrid_add adds the predictions to what the output holds: prior + degrid(G)."""
+    t, dl, uvd, visd, model = case
+    p = lmg.Plan(t, n_img, dl, uvd.shape[0])
+    p.bin(uvd)
+    G = torch.from_numpy(S.random_image(N, 11).astype(np.complex64)).cuda()
+    ref = p.degrid(G)
+    prior = torch.from_numpy(S.complex_normal(uvd.shape[0], 12).astype(np.complex64)).cuda()
+    out = prior.clone()
+    p.degrid(G, out=out, add=True)
+    assert rel_rms((out - prior).cpu().numpy(), ref.cpu().numpy()) < 1e-6
+    z = torch.zeros_like(prior)
+    assert torch.equal(p.degrid(G, out=z, add=True), ref)   # onto zeros: the same bits
