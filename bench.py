@@ -53,7 +53,7 @@ CLOCK_WINDOW_S = 2.2  # the clock record spans the timed steps plus identical st
 VALUE_DEFINITION = ("value = visibilities / time of one whole step (bin + grid + image transform with correction "
                     "and crop + model transform with pad and correction + degrid); grid_degrid_mvis_s = visibilities / "
                     "(grid + degrid kernel time), the narrower figure of the metric's name")
-KERNELS_PER_STEP = 13  # bin 6, grid sweep + spill 2, image transform 2, model transform 2, degrid sweep 1
+KERNELS_PER_STEP = 12  # bin 5, grid sweep + spill 2, image transform 2, model transform 2, degrid sweep 1
 
 
 def parse():
