@@ -499,26 +499,8 @@ def run_native(args):
         torch.distributed.barrier()
     step_ms = max_over_ranks(float(np.mean([s.elapsed_time(e) for s, e in zip(starts, ends)])), dev)
     value = whole_job_mvis(nv, world, step_ms)
-    # The K timed steps of this workload last about K ms, too short for a clock record of
-    # nvidia-smi samples, so identical steps (L2 flushed the same way) continue right after
-    # them until the window is CLOCK_WINDOW_S long; the clocks are taken over the whole
-    # window and the soak's own time per step is reported beside the timed one.
-    soak_n, soak_ms = 0, []
-    t_soak = time.perf_counter()
-    while time.perf_counter() - t_soak + t_wall < CLOCK_WINDOW_S:
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        for _ in range(50):
-            flush.zero_()
-            a.record(stream)
-            step()
-            b.record(stream)
-        torch.cuda.synchronize()
-        soak_ms.append(a.elapsed_time(b))
-        soak_n += 50
-    clk = clocks.stop()
-    clk["window"] = (f"{args.steps} timed steps followed by {soak_n} identical steps "
-                     f"({t_wall + time.perf_counter() - t_soak:.2f} s of steps)")
-    clk["soak_ms_per_step"] = float(np.mean(soak_ms)) if soak_ms else None
+    # the K timed steps last about K ms: the clock record continues over identical steps
+    clk = soak(step, flush, stream, torch, t_wall, clocks, args.steps)
 
     # per-stage breakdown (untimed by the driver's clock; same stream, events per stage)
     stages = {}
@@ -728,6 +710,32 @@ def _events_ms(step, steps, flush, stream, torch):
     return float(np.mean([s.elapsed_time(e) for s, e in zip(starts, ends)]))
 
 
+def soak(step, flush, stream, torch, t_wall, clocks, steps):
+    """Timed steps are often shorter than a useful clock record (nvidia-smi samples every
+    100 ms or so): identical steps (L2 flushed the same way) continue after them until the
+    window is CLOCK_WINDOW_S long. Stops the clock sampler and returns its record with the
+    window and the soak's own time per step."""
+    n, per = 0, []
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 + t_wall < CLOCK_WINDOW_S:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 0
+        a.record(stream)
+        while reps < 50 and time.perf_counter() - t0 + t_wall < CLOCK_WINDOW_S:
+            flush.zero_()
+            step()
+            reps += 1
+        b.record(stream)
+        torch.cuda.synchronize()
+        per.append(a.elapsed_time(b) / reps)
+        n += reps
+    clk = clocks.stop()
+    clk["window"] = (f"{steps} timed steps followed by {n} identical steps "
+                     f"({t_wall + time.perf_counter() - t0:.2f} s of steps)")
+    clk["soak_ms_per_step"] = float(np.mean(per)) if per else None
+    return clk
+
+
 def run_channels(args):
     """Batched channels: tuned, graph-captured batch against sequential single plans."""
     import torch
@@ -775,7 +783,7 @@ def run_channels(args):
     t_wall = time.perf_counter()
     ms_b = _events_ms(batched, args.steps, flush, stream, torch)
     t_wall = time.perf_counter() - t_wall
-    clk = clocks.stop()
+    clk = soak(batched, flush, stream, torch, t_wall, clocks, args.steps)
     ms_s = _events_ms(sequential, args.steps, flush, stream, torch)
     # same accuracy: the batched outputs against the sequential ones
     batched()
@@ -899,8 +907,10 @@ def run_autograd(args):
     clocks = Clocks(0)
     clocks.start()
     clocks.mark()
+    t_wall = time.perf_counter()
     ms_b = _events_ms(batched, args.steps, flush, stream, torch)
-    clk = clocks.stop()
+    t_wall = time.perf_counter() - t_wall
+    clk = soak(batched, flush, stream, torch, t_wall, clocks, args.steps)
     ms_p = _events_ms(per_channel, args.steps, flush, stream, torch)
     gb, gp = grads["batched"].double(), grads["per_channel"].double()
     diff = float(torch.linalg.vector_norm(gb - gp) / torch.linalg.vector_norm(gp))
@@ -984,10 +994,17 @@ def run_large(args):
     clocks = Clocks(0)
     clocks.start()
     clocks.mark()
+    t_wall = time.perf_counter()
     ms_plain = _events_ms(lambda: p32.grid(v64, out=grid), steps, flush, stream, torch)
     ms_comp = _events_ms(lambda: p32.grid(v64, accum="compensated", out=grid), steps, flush, stream, torch)
     ms_degrid = _events_ms(lambda: p32.degrid(grid, out=out), steps, flush, stream, torch)
-    clk = clocks.stop()
+    t_wall = time.perf_counter() - t_wall
+
+    def large_step():
+        p32.grid(v64, out=grid)
+        p32.degrid(grid, out=out)
+
+    clk = soak(large_step, flush, stream, torch, t_wall, clocks, 3 * steps)
     c = a["crop"]
     sl = slice(a["n_image"] // 2 - c // 2, a["n_image"] // 2 + c // 2)
     img_plain = p32.dirty_image(v64)[sl, sl].cpu().numpy()
@@ -1068,15 +1085,30 @@ def run_precision(args):
         g = torch.empty((WORKLOAD["N"], WORKLOAD["N"]), dtype=cd, device=dev)
         vo = torch.empty_like(v)
         reps = max(3, min(args.steps, 10))
+        plan.grid(v, out=g)
+        plan.degrid(g, out=vo)
+        torch.cuda.synchronize()
+        clocks = Clocks(0)
+        clocks.start()
+        clocks.mark()
+        t_wall = time.perf_counter()
         tg = _events_ms(lambda: plan.grid(v, out=g), reps, flush, stream, torch)
         plan.grid(v, out=g)
         td = _events_ms(lambda: plan.degrid(g, out=vo), reps, flush, stream, torch)
+        t_wall = time.perf_counter() - t_wall
+
+        def case_step():
+            plan.grid(v, out=g)
+            plan.degrid(g, out=vo)
+
+        clk = soak(case_step, flush, stream, torch, t_wall, clocks, 2 * reps)
+        plan.grid(v, out=g)
         plan.degrid(g, out=vo)
         torch.cuda.synchronize()
         gi = g.cpu().numpy()[::64, ::64].astype(np.complex128)
         key = (W,)
         row = {"dtype": dt, "W": W, "interp": interp, "oversample": Ms, "grid_ms": tg, "degrid_ms": td,
-               "grid_degrid_mvis_s": nv / ((tg + td) * 1e-3) / 1e6}
+               "grid_degrid_mvis_s": nv / ((tg + td) * 1e-3) / 1e6, "clocks": clk}
         if key in ref:  # agreement of the grid with the first float64 case of the same W
             r = ref[key]
             row["grid_rel_diff_vs_" + r[0]] = float(np.sqrt(np.mean(np.abs(gi - r[1]) ** 2) / np.mean(np.abs(r[1]) ** 2)))
