@@ -10,6 +10,7 @@ import pytest
 
 from oracle import design as D
 from oracle import imaging as I
+from tests import prolate as P
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "lmg.h")
@@ -77,6 +78,22 @@ def test_library_table_matches_oracle(lmg, W, Ms, interp):
     hv = t.correction(n_img)
     hvo = D.correction_factors(Co, Ms, {"nearest": 0, "linear": 1, "cubic": 3}[interp], W, I.pixel_coords(n_img, N))
     np.testing.assert_allclose(hv, hvo, rtol=1e-6)
+
+
+@pytest.mark.parametrize("x0p", [0.1, 0.25, 0.4])
+def test_w1_library_table_is_the_prolate_spheroidal_function(lmg, x0p):
+    """The library's own optimiser at W = 1 against the closed form of tests/prolate.py
+    (E_min = 1 - lambda_0(pi x0) / (2 x0); h and C follow S_00): within the second-order
+    gap of Appendix A's 33 x-nodes and 16 s-nodes (the oracle's side is pinned the same
+    way, with its convergence, in test_oracle_design.py)."""
+    E_ref, h_ref, C_ref = P.w1_design(x0p)
+    Ms = 100
+    C, h, E, info = lmg.Table(1, 2 * x0p, Ms, "linear").export()
+    assert info[0] == 1 and info[2] == 32
+    assert abs(E / E_ref - 1.0) < 1e-3
+    assert np.abs(h - h_ref(x0p * np.arange(33) / 32)).max() < 3e-4
+    t = np.arange(Ms + 1) / Ms - 0.5                   # row i: offset d = i / Ms - 1/2
+    assert np.abs(C[:, 0] / C[Ms // 2, 0] - C_ref(t)).max() < 2e-4
 
 
 def test_w7_library_table_reaches_paper_level(lmg):

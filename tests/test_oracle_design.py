@@ -13,6 +13,8 @@ import pytest
 
 from oracle import design as D
 
+from tests import prolate as P
+
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_claims.json")
 X0P = 0.25  # the paper's recommended x0 (half width); the API's kept fraction 0.5
 
@@ -75,6 +77,29 @@ def test_lm_optimum_is_stationary_in_h(W):
     h_new = a.real.sum(0) / (np.abs(a) ** 2).sum(0)
     h_new /= h_new[x.size // 2]
     assert np.max(np.abs(h_new - h) / h) < 1e-6
+
+
+@pytest.mark.parametrize("x0p", [0.1, 0.25, 0.4])
+def test_w1_design_is_the_prolate_spheroidal_function(x0p):
+    """At W = 1 the least-misfit problem is the prolate spheroidal eigenproblem (derivation
+    in tests/prolate.py): E_min = 1 - lambda_0(pi x0) / (2 x0), h(x) follows S_00(pi x0, x/x0)
+    and C(t) follows S_00(pi x0, 2t). The oracle's discretised optimum (2Ng+1 trapezoid
+    x-nodes and Mg midpoint s-nodes, Appendix A) approaches all three at second order:
+    each gap shrinks about fourfold when Ng and Mg double."""
+    c = np.pi * x0p
+    assert abs(P.lambda0_nystrom(c) - P.lambda0_from_pro_ang1(c)) < 1e-12
+    E_ref, h_ref, C_ref = P.w1_design(x0p)
+    t = np.linspace(-0.5, 0.5, 41)                     # offsets d = s - 1/2
+    gaps = []
+    for Ng, Mg in [(32, 16), (64, 32)]:
+        h = D.least_misfit_h(1, x0p, Ng, Mg)
+        E = D.design_E(h, 1, x0p, Ng, Mg)
+        C = D.exact_C(h, 1, x0p, t + 0.5, Ng, Mg)[:, 0]
+        C0 = D.exact_C(h, 1, x0p, np.array([0.5]), Ng, Mg)[0, 0]
+        xn = x0p * np.arange(Ng + 1) / Ng
+        gaps.append(np.array([abs(E / E_ref - 1.0), np.abs(h - h_ref(xn)).max(), np.abs(C / C0 - C_ref(t)).max()]))
+    assert np.all(gaps[0] < [1e-3, 3e-4, 2e-4])
+    assert np.all(gaps[1] < 0.35 * gaps[0])
 
 
 def test_lm_optimum_is_a_minimum():
