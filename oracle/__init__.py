@@ -21,12 +21,13 @@ Library primitives used as single steps: ``scipy.optimize.leastsq`` (MINPACK
 Levenberg-Marquardt, the routine the paper names in Appendix A), ``scipy.linalg`` Cholesky
 and triangular solves, ``numpy.linalg.qr`` (Householder QR, Appendix B) and ``numpy.fft``.
 
-Parity status: at support W = 1 the design reduces exactly to the prolate spheroidal
-eigenproblem (E_min = 1 - lambda_0(pi x0) / (2 x0), h and C proportional to the angular
-function S_00), and C(u), h(x) and E are pinned there against scipy's ``pro_ang1`` and the
-sinc-kernel eigenvalue, with second-order convergence in the node counts
-(tests/prolate.py). For W >= 2 the paper prints no values (its figures are lost): the
-exact values of C(u) and h(x) are **parity unpinned** there, and pinned indirectly by
+Parity status: C(u), h(x) and E are pinned by closed forms in two limits (tests/prolate.py,
+tests/small_field.py): at support W = 1 the design is exactly the prolate spheroidal
+eigenproblem (E_min = 1 - lambda_0(pi x0) / (2 x0), h and C proportional to S_00), and for
+W = 1..4 on a small field the optimum has a moment-matching closed form (rational even
+moments, E proportional to (2 pi x0)^(2W)); the oracle approaches both at second order. At
+the working x0 and W >= 5 the paper prints no values (its figures are lost): there the
+exact values of C(u) and h(x) are **parity unpinned**, and pinned indirectly by
 stationarity, by the paper's ordering and bound claims and by route agreement (see
 tests/test_oracle_*.py).
 """

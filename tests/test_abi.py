@@ -11,6 +11,7 @@ import pytest
 from oracle import design as D
 from oracle import imaging as I
 from tests import prolate as P
+from tests import small_field as SF
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "lmg.h")
@@ -94,6 +95,19 @@ def test_w1_library_table_is_the_prolate_spheroidal_function(lmg, x0p):
     assert np.abs(h - h_ref(x0p * np.arange(33) / 32)).max() < 3e-4
     t = np.arange(Ms + 1) / Ms - 0.5                   # row i: offset d = i / Ms - 1/2
     assert np.abs(C[:, 0] / C[Ms // 2, 0] - C_ref(t)).max() < 2e-4
+
+
+@pytest.mark.parametrize("W", [2, 3, 4])
+def test_library_table_small_field_limit(lmg, W):
+    """The library's own optimiser at x0 = 0.025 (API 0.05) against the small-field closed
+    form of tests/small_field.py: E within 1%, C within 1.5e-3, h's deviation from 1 within
+    1% (the oracle's side, with its convergence, is in test_oracle_design.py)."""
+    x0p, Ms = 0.025, 100
+    C, h, E, _ = lmg.Table(W, 2 * x0p, Ms, "linear").export()
+    assert abs(E / SF.E_leading(W, x0p) - 1.0) < 0.01
+    Cp = SF.C_leading(W, np.arange(Ms + 1) / Ms)
+    assert np.abs(C - Cp).max() < 1.5e-3 * np.abs(Cp).max()
+    assert np.abs(h - SF.h_leading(W, x0p * np.arange(33) / 32)).max() < 1e-2 * np.abs(h - 1.0).max()
 
 
 def test_w7_library_table_reaches_paper_level(lmg):

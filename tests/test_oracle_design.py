@@ -14,6 +14,7 @@ import pytest
 from oracle import design as D
 
 from tests import prolate as P
+from tests import small_field as SF
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_claims.json")
 X0P = 0.25  # the paper's recommended x0 (half width); the API's kept fraction 0.5
@@ -100,6 +101,31 @@ def test_w1_design_is_the_prolate_spheroidal_function(x0p):
         gaps.append(np.array([abs(E / E_ref - 1.0), np.abs(h - h_ref(xn)).max(), np.abs(C / C0 - C_ref(t)).max()]))
     assert np.all(gaps[0] < [1e-3, 3e-4, 2e-4])
     assert np.all(gaps[1] < 0.35 * gaps[0])
+
+
+@pytest.mark.parametrize("W", [1, 2, 3, 4])
+def test_small_field_limit_of_the_design(W):
+    """As x0 -> 0 the optimum of every W has a closed form (derivation in
+    tests/small_field.py): C(s) matches the moments of 1/h on the support offsets, the
+    free even moments (e.g. 17/60 at W = 3, 8/21 at W = 4) minimise the s-average of the
+    leading moment, and E follows (2 pi x0)^(2W) with a monic-Legendre factor. The oracle
+    reaches E, C and h of that form with O(x0^2) relative gaps: a design that skipped the
+    optimisation of h, or a wrong support offset or normalisation of E, misses E by large
+    factors."""
+    out = {}
+    for x0p in (0.05, 0.025):
+        h = D.least_misfit_h(W, x0p)
+        E = D.design_E(h, W, x0p)
+        s = np.linspace(0.0, 1.0, 41)
+        C, Cp = D.exact_C(h, W, x0p, s), SF.C_leading(W, s)
+        hp = SF.h_leading(W, x0p * np.arange(h.size) / (h.size - 1))
+        out[x0p] = (abs(E / SF.E_leading(W, x0p) - 1.0), np.abs(C - Cp).max() / np.abs(Cp).max(),
+                    np.abs(h - hp).max() / np.abs(h - 1.0).max())
+    (e1, c1, h1), (e2, c2, h2) = out[0.05], out[0.025]
+    assert e1 < 0.08 and e2 < 0.01
+    assert c1 < 5e-3 and c2 < 1.5e-3 and c2 < 0.4 * c1
+    if W >= 2:                                         # W = 1: h = 1 + O(x0^2) only
+        assert h1 < 1e-2 and h2 < 1e-2
 
 
 def test_lm_optimum_is_a_minimum():
