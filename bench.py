@@ -502,7 +502,7 @@ def run_native(args):
     # the K timed steps last about K ms: the clock record continues over identical steps
     clk = soak(step, flush, stream, torch, t_wall, clocks, args.steps)
 
-    # per-stage breakdown (untimed by the driver's clock; same stream, events per stage)
+    # per-stage breakdown (outside the timed steps; same stream, events per stage)
     stages = {}
 
     def timed(name, fn, reps=max(3, min(args.steps, 10))):

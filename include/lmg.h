@@ -60,7 +60,7 @@ typedef enum {
   LMG_ENOMEM = -2,        /* host or device allocation failed */
   LMG_ECUDA = -3,         /* a CUDA runtime call or kernel launch failed */
   LMG_ECUFFT = -4,        /* a cuFFT call failed */
-  LMG_EUNSUPPORTED = -5,  /* valid request this build does not implement */
+  LMG_EUNSUPPORTED = -5,  /* valid request that this library does not implement */
   LMG_ENOCONV = -6,       /* the least-misfit optimisation did not converge */
   LMG_EDEVICE = -7        /* a kernel's own check found an anomaly (lmg_plan_status) */
 } lmg_status;
