@@ -15,7 +15,11 @@
 //      KC column weights: Cu_i w V (gridding) or Cu_i (degridding). Slot (lane mod PS) of a
 //      record belongs to the lane that reads it, so no lane needs the record's start column;
 //   2. each lane builds the set of records whose support covers one of its columns (32x32
-//      bit transpose of the per-record lane masks) and visits them, two per iteration;
+//      bit transpose of the per-record lane masks) and visits them, two per iteration.
+//      Degridding stages and transposes once per window of 32 consecutive records (lane l
+//      holding record l, whatever row pair it belongs to; row pairs start at even rows, so
+//      d = row & 1) and visits each chunk's part of the window's set: the same records in
+//      the same order, with a window that spans several sparse row pairs staged once;
 //   3. gridding: lane t holds a ring of RS >= TP accumulator rows for each of its columns in
 //      registers, as pairs of rows (one f32x2 register per pair for complex64), and adds
 //      (Cv'_q, Cv'_q+1) x (a, a) with one packed FMA per pair and per real/imaginary part --
@@ -416,6 +420,10 @@ __device__ __forceinline__ unsigned lane_range_mask(int L0, int L1) {
   if (a > b) return 0u;
   return (0xffffffffu >> (31 - b)) & (0xffffffffu << a);
 }
+// Bits a .. b - 1 of a window's record mask (0 <= a < b <= 32).
+__device__ __forceinline__ unsigned record_range(int a, int b) {
+  return (b >= 32 ? 0xffffffffu : ((1u << b) - 1u)) & ~((1u << a) - 1u);
+}
 template <int W, int KC> __device__ __forceinline__ unsigned cover_lanes(int xrel) {
   return lane_range_mask(xrel >> (KC - 1), (xrel + W - 1) >> (KC - 1));
 }
@@ -804,6 +812,8 @@ __device__ __forceinline__ void degrid_item(const SweepArgs& a, const R* __restr
   const int rb = off[item.r0], rend = off[item.r1];
   int pend = pair_ends(off, item, 0, lane);
   int wbase = rb, cstart = rb;
+  int staged = -1;    // window whose records are staged
+  unsigned MW = 0u;   // records of that window covering this lane's columns
   Rec rc0{0u, 0, 0u, 0u}, rc1{0u, 0, 0u, 0u}, rc2{0u, 0, 0u, 0u};
   if (rb + lane < rend) rc0 = recs[rb + lane];
   if (rb + 32 + lane < rend) rc1 = recs[rb + 32 + lane];
@@ -813,25 +823,31 @@ __device__ __forceinline__ void degrid_item(const SweepArgs& a, const R* __restr
     for (int gp = 0; gp < NP; ++gp) {
       const int gb = g0 + gp * kD;
       if (gb < nrows) {
-        const int row0 = item.r0 + gb;
         put_pair((gp + NPR - 1) % RH);
         fetch_pair(gb + 2 * NPR);
         if (gb > 0 && (gb & 63) == 0) pend = pair_ends(off, item, gb >> 6, lane);
         const int re = __shfl_sync(0xffffffffu, pend, (gb & 63) >> 1);
         while (cstart < re) {
           const int ce = min(re, wbase + 32);
-          const bool mine = lane >= cstart - wbase && lane < ce - wbase;
           const int xrel = rec_xrel(rc0.rx);
-          if (mine) {
-            int ou, ov;
-            R fu, fv;
-            record_coords<R, EXT>(a, rc0, ou, fu, ov, fv);
-            stage_degrid<W, R, EXT>(tab, Wp, a.interp, ou, fu, ov, fv, rec_row(rc0.rx) - row0, xrel, s_cv, s_u,
-                                    lane);
+          if (staged != wbase) {
+            // every record of the window is staged once, by its own lane, whatever row pair
+            // it belongs to: row pairs start at even rows, so its Cv' shift is row & 1
+            __syncwarp();  // the previous window's staging and partial sums have been read
+            const bool valid = wbase + lane < rend;
+            if (valid) {
+              int ou, ov;
+              R fu, fv;
+              record_coords<R, EXT>(a, rc0, ou, fu, ov, fv);
+              stage_degrid<W, R, EXT>(tab, Wp, a.interp, ou, fu, ov, fv, rec_row(rc0.rx) & 1, xrel, s_cv, s_u,
+                                      lane);
+            }
+            MW = transpose32(valid ? cover_lanes<W, KC>(xrel) : 0u, lane);
+            staged = wbase;
+            __syncwarp();
           }
-          const unsigned cover = mine ? cover_lanes<W, KC>(xrel) : 0u;
-          __syncwarp();
-          unsigned M = transpose32(cover, lane);
+          const bool mine = lane >= cstart - wbase && lane < ce - wbase;
+          unsigned M = MW & record_range(cstart - wbase, ce - wbase);
           while (M) {
             const int l1 = __ffs(M) - 1;
             M &= M - 1u;
@@ -902,7 +918,6 @@ __device__ __forceinline__ void degrid_item(const SweepArgs& a, const R* __restr
             // (two terms onto zero: the sum does not depend on their order)
             red_add(out + rc0.idx, o);
           }
-          __syncwarp();
           cstart = ce;
           if (cstart == wbase + 32) {
             wbase += 32;
