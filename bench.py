@@ -339,12 +339,15 @@ def sweep_sources_sha256():
 
 def traffic_record(pass_name):
     """DRAM traffic per launch of the gridding ("grid") or degridding ("degrid") sweep from
-    the committed ncu summary, if it was taken on the current sweep sources."""
+    the committed ncu summary, if the pass's record holds for the current sweep sources
+    (the SHA-256 of the sources it was taken on, or of later sources that left that pass's
+    kernel code unchanged, listed in the record with the reason)."""
     p = os.path.join(ROOT, "profiles", "sweeps_config2_traffic.json")
     try:
         with open(p) as f:
             rec = json.load(f)
-        if rec.get("sweep_sources_sha256") != sweep_sources_sha256():
+        valid = rec[pass_name].get("sources_sha256", [rec.get("sweep_sources_sha256")])
+        if sweep_sources_sha256() not in valid:
             return None
         return float(rec[pass_name]["traffic_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
