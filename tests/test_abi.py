@@ -97,6 +97,18 @@ def test_w1_library_table_is_the_prolate_spheroidal_function(lmg, x0p):
     assert np.abs(C[:, 0] / C[Ms // 2, 0] - C_ref(t)).max() < 2e-4
 
 
+@pytest.mark.parametrize("x0p", [0.1, 0.25, 0.4])
+def test_w1_library_correction_is_prolate(lmg, x0p):
+    """The library's correction factors (its own quadrature of c and D, Eqs. 12-15) for its
+    W = 1 table follow S_00(pi x0, x/x0) on the kept pixels (closed form in tests/prolate.py)."""
+    _, h_ref, _ = P.w1_design(x0p)
+    n_img = 64
+    N = int(round(n_img / (2 * x0p)))
+    hv = lmg.Table(1, 2 * x0p, 1000, "linear").correction(n_img)
+    x = I.pixel_coords(n_img, N)
+    assert np.abs(hv / hv[n_img // 2] - h_ref(x)).max() < 2e-5
+
+
 @pytest.mark.parametrize("W", [2, 3, 4])
 def test_library_table_small_field_limit(lmg, W):
     """The library's own optimiser at x0 = 0.025 (API 0.05) against the small-field closed

@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 from oracle import design as D
+from oracle import imaging as I
 
 from tests import prolate as P
 from tests import small_field as SF
@@ -101,6 +102,21 @@ def test_w1_design_is_the_prolate_spheroidal_function(x0p):
         gaps.append(np.array([abs(E / E_ref - 1.0), np.abs(h - h_ref(xn)).max(), np.abs(C / C0 - C_ref(t)).max()]))
     assert np.all(gaps[0] < [1e-3, 3e-4, 2e-4])
     assert np.all(gaps[1] < 0.35 * gaps[0])
+
+
+@pytest.mark.parametrize("x0p", [0.1, 0.25, 0.4])
+def test_w1_correction_factors_are_prolate(x0p):
+    """At W = 1 the optimal correction c/D of Eqs. 12-15 is K C / ||C||^2 with K the cosine
+    kernel of tests/prolate.py, so for the designed C it follows S_00(pi x0, x/x0) across
+    the kept field; K damps the part of C that is not prolate, so the factors of the
+    tabulated function meet the closed form far more closely than C does."""
+    _, h_ref, _ = P.w1_design(x0p)
+    n_img = 64
+    N = int(round(n_img / (2 * x0p)))
+    x = I.pixel_coords(n_img, N)
+    T = D.lm_table(D.least_misfit_h(1, x0p), 1, x0p, 1000)
+    hv = D.correction_factors(T, 1000, D.INTERP_LINEAR, 1, x)
+    assert np.abs(hv / hv[n_img // 2] - h_ref(x)).max() < 2e-5
 
 
 @pytest.mark.parametrize("W", [1, 2, 3, 4])
