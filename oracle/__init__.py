@@ -24,10 +24,11 @@ and triangular solves, ``numpy.linalg.qr`` (Householder QR, Appendix B) and ``nu
 Parity status: C(u), h(x) and E are pinned by closed forms in two limits (tests/prolate.py,
 tests/small_field.py): at support W = 1 the design is exactly the prolate spheroidal
 eigenproblem (E_min = 1 - lambda_0(pi x0) / (2 x0), h and C proportional to S_00), and for
-W = 1..4 on a small field the optimum has a moment-matching closed form (rational even
-moments, E proportional to (2 pi x0)^(2W)); the oracle approaches both at second order. At
-the working x0 and W >= 5 the paper prints no values (its figures are lost): there the
-exact values of C(u) and h(x) are **parity unpinned**, and pinned indirectly by
-stationarity, by the paper's ordering and bound claims and by route agreement (see
-tests/test_oracle_*.py).
+W = 1..5 on a small field the optimum has a moment-matching closed form (rational even
+moments, E proportional to (2 pi x0)^(2W)); the oracle approaches both at second order
+(W = 5 through the least-squares route of Appendix B, which keeps the digits there). At
+the working x0 (0.25) the paper prints no values (its figures are lost), so for W >= 2 the
+exact values of C(u) and h(x) there are **parity unpinned**: the same code is pinned in
+those limits (for W <= 5), and the values themselves only indirectly, by stationarity, by
+the paper's ordering and bound claims and by route agreement (see tests/test_oracle_*.py).
 """

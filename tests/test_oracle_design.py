@@ -144,6 +144,32 @@ def test_small_field_limit_of_the_design(W):
         assert h1 < 1e-2 and h2 < 1e-2
 
 
+def test_small_field_limit_w5_through_least_squares(monkeypatch):
+    """W = 5 meets the small-field closed form only near x0 = 0.01, where E ~ 1e-24: there
+    the normal equations (whose condition number is that of Appendix B's least-squares
+    matrix, squared) leave float64 no digits, so the design runs on the least-squares route
+    that Appendix B introduces for this loss of precision. E approaches the closed form at
+    second order (within 10% at x0 = 0.025, 1% at 0.0125) and C and h follow it."""
+    monkeypatch.setattr(D, "QR_ABOVE_W", 0)
+    D._least_misfit_h.cache_clear()
+    try:
+        W = 5
+        gaps = {}
+        for x0p in (0.025, 0.0125):
+            h = D.least_misfit_h(W, x0p)
+            E = D.design_E(h, W, x0p)
+            s = np.linspace(0.0, 1.0, 41)
+            C, Cp = D.exact_C(h, W, x0p, s), SF.C_leading(W, s)
+            hp = SF.h_leading(W, x0p * np.arange(h.size) / (h.size - 1))
+            gaps[x0p] = (abs(E / SF.E_leading(W, x0p) - 1.0), np.abs(C - Cp).max() / np.abs(Cp).max(),
+                         np.abs(h - hp).max() / np.abs(h - 1.0).max())
+        assert gaps[0.025][0] < 0.1 and gaps[0.0125][0] < 0.01
+        assert gaps[0.025][1] < 1.5e-3 and gaps[0.0125][1] < 1e-3
+        assert gaps[0.025][2] < 3e-3 and gaps[0.0125][2] < 2e-3
+    finally:
+        D._least_misfit_h.cache_clear()
+
+
 def test_lm_optimum_is_a_minimum():
     """Random perturbations of h(x_1..x_Ng) never lower E."""
     W = 6
