@@ -188,19 +188,24 @@ int lmg_plan_dropped(lmg_plan* p, int64_t* dropped, void* stream);
  *   accum    LMG_ACCUM_PLAIN, or LMG_ACCUM_COMPENSATED (C64 only: each accumulator is
  *            a float pair updated with an error-free sum)
  *   grid     device complex [N][N]; every cell is overwritten (no pre-zeroing needed)
- * Allocates nothing. */
+ * Allocates nothing. Where work items are shorter than W - 1 rows (dense rows), the partial
+ * rows of two items are added into the same cells by atomics in either order, so two calls
+ * on the same input may differ at the rounding level of the dtype. */
 int lmg_grid(lmg_plan* p, const void* vis, const void* weights, int accum, void* grid,
              void* stream);
 
 /* lmg_degrid -- V_k = sum_{i,j} C(n_i - u_k) C(m_j - v_k) G[m_j][n_i] (Section 4, the
  * transpose of lmg_grid without weights). grid: device complex [N][N];
- * vis_out: device complex [nvis], every entry overwritten. Allocates nothing. */
+ * vis_out: device complex [nvis], every entry overwritten. Allocates nothing. The result
+ * is the same bits on every call (each entry is one sum, or two added onto zero when the
+ * support crosses a 64-column strip, 32 for complex128). */
 int lmg_degrid(lmg_plan* p, const void* grid, void* vis_out, void* stream);
 
 /* lmg_degrid_add -- lmg_degrid that adds the predictions to vis_inout instead of
  * overwriting it (Section 4; e.g. the sum of the predictions from several grids, or an
  * output zeroed earlier on another stream). Dropped positions leave their entries as they
- * are. Same arguments, alignment and errors as lmg_degrid. */
+ * are. Same arguments, alignment and errors as lmg_degrid. The two adds of a visibility
+ * whose support crosses a strip may land in either order. */
 int lmg_degrid_add(lmg_plan* p, const void* grid, void* vis_inout, void* stream);
 
 /* lmg_fft -- unnormalised in-place 2-D FFT of a device grid [N][N] in grid index order.
