@@ -170,6 +170,14 @@ def test_small_field_limit_w5_through_least_squares(monkeypatch):
         D._least_misfit_h.cache_clear()
 
 
+def test_design_constants_are_the_papers():
+    """The node counts of Appendix A and the route threshold of Appendix E, as the oracle
+    uses them, are the values the paper states (golden file)."""
+    c = claims()
+    assert (D.NG_DEFAULT, D.MG_DEFAULT) == (c["design_grid"]["Ng"], c["design_grid"]["Mg"])
+    assert D.QR_ABOVE_W == c["qr_above_W"]["value"]
+
+
 def test_lm_optimum_is_a_minimum():
     """Random perturbations of h(x_1..x_Ng) never lower E."""
     W = 6
@@ -286,6 +294,8 @@ def test_interpolation_error_order():
         T = D.lm_table(h, W, X0P, Ms)
         for d in range(4):
             errs[d].append(np.abs(D.table_weights(T, Ms, s, d) - exact).max())
+    law = claims()["interp_error_exponent"]               # the paper's exponents for d = 0, 1
+    assert law["nearest"] == 1 and law["linear"] == 2
     for d in range(4):
         p = np.log2(errs[d][0] / errs[d][2]) / 2
         assert abs(p - (d + 1)) < 0.2, (d, p)
